@@ -1,0 +1,368 @@
+"""Benchmark: RHS solved per second at a 1e-8 FP64 true residual, 24^3x64 Wilson lattice.
+
+One step is one pass of the whole hot path over one batch of synthetic input:
+  1. eigCG(10, 100) on one new RHS, deflated by the resident basis (Eq. 1 + Fig. 1),
+     then basis_grow (Sec. 4 box) and a rollback of the basis to its base size so
+     that every step does the same work;
+  2. init-CG on a batch of k = 16 RHS through the multi-RHS dslash, deflated by the
+     basis and restarted once at 1e-6 (Sec. 5.3).
+Storage FP32 (12-real links) with FP64 reliable updates and FP64 true residuals.
+The basis (up to 240 vectors, as in Sec. 5) is grown by Incremental eigCG before
+the warm-up steps.  Inputs are synthetic (gauge recipe and Gaussian RHS of the
+fixtures module), every field far larger than L2.
+
+Also reported: plain FP64 eigCG (no deflation, no batching, FP64 storage) on the
+same GPU, the dominant kernel's roofline, the end-to-end rate through the C ABI
+with host buffers, and the FP64 CPU oracle's rate on the host cores.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_0707_0131_gb300 import fixtures as fx  # noqa: E402
+
+METRIC = "RHS solved/s at 1e-8 residual (24^3x64)"
+UNIT = "RHS/s"
+LATTICE = "24^3x64"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--lattice", default=LATTICE)
+    ap.add_argument("--k", type=int, default=16)
+    ap.add_argument("--basis", type=int, default=240)
+    ap.add_argument("--nev", type=int, default=10)
+    ap.add_argument("--m", type=int, default=100)
+    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--restart-tol", type=float, default=1e-6)
+    ap.add_argument("--kappa", default="1e+05")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def mass_for(lattice, kappa):
+    masses = json.load(open(os.path.join(ROOT, "configs", "masses.json")))
+    if lattice in masses and kappa in masses[lattice]:
+        return masses[lattice][kappa]["m_q"], f"{lattice} calibration"
+    # bulk critical mass of this gauge recipe is volume independent: take the
+    # largest calibrated lattice's mass for the same target condition number
+    for name in ("16^3x32", "8^4"):
+        if name in masses and kappa in masses[name]:
+            return masses[name][kappa]["m_q"], f"{name} calibration"
+    raise KeyError(f"no mass for {lattice} cond {kappa}")
+
+
+def rank_info():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append([v.strip() for v in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm = [float(s[0]) for s in self.samples if len(s) >= 8 and s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if len(s) >= 8 and s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for s in self.samples:
+            if len(s) < 8:
+                continue
+            for i, n in enumerate(names):
+                if s[4 + i].lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_rate(dims, m_q, gauge, seconds):
+    """FP64 CPU oracle: seconds per CG iteration (one A application + vector updates)."""
+    import oracle
+    from oracle import solvers
+
+    W = oracle.Wilson(dims, m_q, gauge)
+    b = fx.make_rhs(dims, fx.rhs_seed(LATTICE if tuple(dims) == fx.LATTICES[LATTICE] else "8^4", 999))[0]
+    t0 = time.perf_counter()
+    solvers.cg(W, b, tol=1e-30, max_iter=1)  # warm
+    per = time.perf_counter() - t0
+    n = max(2, int(seconds / max(per, 1e-3)))
+    t0 = time.perf_counter()
+    res = solvers.cg(W, b, tol=1e-30, max_iter=n)
+    dt = time.perf_counter() - t0
+    # cg() also spends one A application on the final true residual
+    return dt / (res["iters"] + 1), res["iters"], oracle.num_threads()
+
+
+def run_reference(a):
+    rank, world, _ = rank_info()
+    if rank != 0:
+        return
+    dims = fx.LATTICES[a.lattice]
+    m_q, _ = mass_for(a.lattice, a.kappa)
+    gauge = fx.make_gauge(dims, fx.GAUGE_SEEDS[a.lattice])
+    cfg = json.load(open(os.path.join(ROOT, "configs", "bench.json")))
+    iters_per_rhs = cfg["iters_per_rhs"]
+    per_step = max(2.0, min(a.cpu_seconds, 60.0) / max(1, a.steps))
+    oracle_rate(dims, m_q, gauge, 1.0)  # warm-up
+    times = []
+    for _ in range(a.steps):
+        t_it, n, cores = oracle_rate(dims, m_q, gauge, per_step)
+        times.append(t_it)
+    t_it = float(np.mean(times))
+    value = 1.0 / (t_it * iters_per_rhs)
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
+           "steps": a.steps, "warmup": a.warmup, "ms_per_step": t_it * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"{a.lattice} Wilson, cond(A)~{a.kappa}, k={a.k}, basis {a.basis}, tol {a.tol}"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": f"FP64 oracle CG iterations on one RHS of the {a.lattice} workload, "
+                                      f"{per_step:.0f} s per step; RHS/s = 1/(s per iteration x "
+                                      f"{iters_per_rhs} iterations per RHS, configs/bench.json)"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+        return
+    import torch
+
+    from paper_0707_0131_gb300 import _lib
+    from paper_0707_0131_gb300.api import Basis, Op
+
+    rank, world, local = rank_info()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    dims = fx.LATTICES[a.lattice]
+    V = fx.volume(dims)
+    m_q, mass_src = mass_for(a.lattice, a.kappa)
+    gauge = fx.make_gauge(dims, fx.GAUGE_SEEDS[a.lattice])
+    k = a.k
+    op = Op(gauge, dims, m_q, prec=32, max_rhs=k)
+    basis = Basis(op, max(a.basis, 16))
+    nrhs_id = [0]
+
+    def next_rhs(n):
+        out = []
+        for _ in range(n):
+            out.append(fx.make_rhs(dims, fx.rhs_seed(a.lattice, 1000 * rank + nrhs_id[0]))[0])
+            nrhs_id[0] += 1
+        return np.stack(out)
+
+    # --- setup: Incremental eigCG until the basis holds a.basis vectors -------------------
+    t0 = time.perf_counter()
+    phase1 = []
+    while basis.size + a.nev <= a.basis:
+        b = torch.from_numpy(next_rhs(1)[0]).to(dev)
+        x = torch.zeros_like(b)
+        st = op.eigcg_solve(b, x, a.nev, a.m, a.tol, basis=basis)
+        basis.grow()
+        phase1.append(st["iters"])
+    setup_s = time.perf_counter() - t0
+    l0 = basis.size
+
+    # step inputs: fresh RHS per step, resident on the device
+    nsteps = a.warmup + a.steps
+    B1 = [torch.from_numpy(next_rhs(1)[0]).to(dev) for _ in range(nsteps)]
+    Bk = [torch.from_numpy(next_rhs(k)).to(dev) for _ in range(nsteps)]
+    iters = {"eigcg": [], "initcg": []}
+    status = {"true_res": []}
+
+    def step(i, b1, x1, bk, xk, record):
+        st = op.eigcg_solve(b1, x1, a.nev, a.m, a.tol, basis=basis)
+        basis.grow()
+        basis.truncate(l0)
+        sts = op.initcg_solve(bk, xk, a.tol, a.restart_tol, basis=basis, k=k)
+        if record:
+            iters["eigcg"].append(st["iters"])
+            iters["initcg"].extend(s["iters"] for s in sts)
+            status["true_res"].extend([st["true_rel_res"]] + [s["true_rel_res"] for s in sts])
+
+    for i in range(a.warmup):
+        step(i, B1[i], torch.zeros_like(B1[i]), Bk[i], torch.zeros_like(Bk[i]), False)
+    X1 = [torch.zeros_like(B1[i]) for i in range(nsteps)]
+    Xk = [torch.zeros_like(Bk[i]) for i in range(nsteps)]
+    clocks = ClockSampler(local)
+    _lib.eig_profile_reset()
+    _lib.eig_profile_enable(True)
+    barrier()
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for i in range(a.warmup, nsteps):
+        step(i, B1[i], X1[i], Bk[i], Xk[i], True)
+    ev1.record()
+    barrier()
+    clk = clocks.stop()
+    _lib.eig_profile_enable(False)
+    prof = _lib.eig_profile_read()
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    rhs_per_step = 1 + k
+    value = world * a.steps * rhs_per_step / (ms / 1e3)
+    launches = int(sum(v["launches"] for v in prof.values()))
+    # dominant kernel roofline (HBM-bound stencil)
+    kern = max((n for n in prof if n.startswith("dslash")), key=lambda n: prof[n]["ms"])
+    kp = prof[kern]
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(peaks_path):
+        peak = json.load(open(peaks_path))["hbm_gbs"]
+        peak_src = "measured"
+    else:
+        peak, peak_src = 6800.0, "fallback"
+    achieved = (kp["bytes"] / kp["launches"]) / (kp["ms"] / kp["launches"] / 1e3) / 1e9
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tfile):
+        tj = json.load(open(tfile))
+        src = open(os.path.join(ROOT, "paper_0707_0131_gb300", "csrc", "dslash.cu"), "rb").read()
+        if tj.get(kern, {}).get("dslash_sha1") == hashlib.sha1(src).hexdigest():
+            traffic = tj[kern]["bytes_per_launch"]
+    roofline = {"bound": "hbm", "kernel": kern, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_src, "traffic": traffic,
+                "algorithmic_bytes_per_launch": kp["bytes"] / kp["launches"],
+                "avg_launch_ms": kp["ms"] / kp["launches"], "launches": kp["launches"]}
+    kernels = {n: {"launches": v["launches"], "ms": round(v["ms"], 3),
+                   "GBps": (v["bytes"] / (v["ms"] / 1e3) / 1e9) if v["ms"] > 0 else None}
+               for n, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}
+
+    # --- end to end: same steps with pinned host buffers -----------------------------
+    e2e = None
+    if not a.no_e2e:
+        hb1 = [torch.from_numpy(next_rhs(1)[0]).pin_memory() for _ in range(a.steps)]
+        hbk = [torch.from_numpy(next_rhs(k)).pin_memory() for _ in range(a.steps)]
+        hx1 = [torch.zeros_like(t).pin_memory() for t in hb1]
+        hxk = [torch.zeros_like(t).pin_memory() for t in hbk]
+        barrier()
+        t0 = time.perf_counter()
+        for i in range(a.steps):
+            step(i, hb1[i], hx1[i], hbk[i], hxk[i], False)
+        barrier()
+        e2e_s = time.perf_counter() - t0
+        bytes_in = (1 + k) * V * 12 * 16 * 2  # b and the initial guess x
+        bytes_out = (1 + k) * V * 12 * 16
+        e2e = {"value": world * a.steps * rhs_per_step / e2e_s, "unit": UNIT, "h2d_bytes_per_step": bytes_in,
+               "d2h_bytes_per_step": bytes_out}
+
+    # --- plain FP64 eigCG on the same GPU ---------------------------------------------
+    plain = None
+    if not a.no_plain:
+        op64 = Op(gauge, dims, m_q, prec=64)
+        b = B1[0]
+        x = torch.zeros_like(b)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = op64.eigcg_solve(b, x, a.nev, a.m, a.tol, max_iter=20000)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        plain = {"value": 1.0 / dt, "unit": UNIT, "iters": st["iters"], "true_rel_res": st["true_rel_res"]}
+        op64.close()
+
+    # --- CPU oracle on a bounded sample ------------------------------------------------
+    cpu = None
+    all_iters = iters["eigcg"] + iters["initcg"]
+    mean_iters = float(np.mean(all_iters))
+    if not a.no_cpu and rank == 0:
+        t_it, n, cores = oracle_rate(dims, m_q, gauge, a.cpu_seconds)
+        cpu = {"value": 1.0 / (t_it * mean_iters), "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{n} FP64 oracle CG iterations on one RHS of this workload ({t_it:.3f} s each); "
+                         f"RHS/s = 1/(s per iteration x {mean_iters:.0f} mean iterations per RHS of the timed steps)"}
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+               "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+               "config": {"workload": f"{a.lattice} Wilson, m_q={m_q} ({mass_src}, cond(A)~{a.kappa}), "
+                                      f"per step 1 eigCG({a.nev},{a.m}) + grow + k={k} batched init-CG, "
+                                      f"basis {l0} FP32 vectors, tol {a.tol}, restart {a.restart_tol}",
+                          "lattice": a.lattice, "k": k, "basis": l0, "storage": "fp32 spinors, 12-real fp32 links, "
+                          "fp64 reliable updates", "l2": "inputs larger than L2 (each field >= 85 MB)",
+                          "parallelism": f"replicas{world}"},
+               "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+               "clocks": clk, "plain_fp64_eigcg": plain,
+               "vs_plain_fp64_eigcg": (value / world / plain["value"]) if plain else None,
+               "iters_per_rhs": {"eigcg_mean": float(np.mean(iters["eigcg"])),
+                                 "initcg_mean": float(np.mean(iters["initcg"])),
+                                 "phase1_first": phase1[0] if phase1 else None, "phase1_last": phase1[-1] if phase1 else None},
+               "max_true_rel_res": float(np.max(status["true_res"])), "setup_s": setup_s, "kernels": kernels}
+        print(json.dumps(out), flush=True)
+    basis.close()
+    op.close()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,166 @@
+/*
+ * eigcg.h -- C ABI of the GB300 incremental-eigCG library (libeigcg.so).
+ *
+ * The library solves many right-hand sides of A x = b for the lattice-QCD normal
+ * operator A = M^H M, M = m_q I - D the Wilson-Dirac matrix (Sec. 1: "the CG on
+ * the A = M^H M Hermitian operator", gamma5 M = M^H gamma5), with
+ *   - eigCG(nev, m): CG plus a restarted window of Lanczos vectors that yields nev
+ *     Ritz pairs per solve (Sec. 3, Fig. 1);
+ *   - Incremental eigCG: Ritz vectors of successive solves accumulate into a
+ *     deflation basis U with H = U^H A U (Sec. 4 box);
+ *   - init-CG: the Galerkin deflated initial guess of Eq. 1, restarted once near
+ *     single precision (Sec. 5.3).
+ *
+ * Operator convention (Sec. 1 fixes only M = m_q I - D and gamma5-Hermiticity):
+ *   (M psi)(x) = (4 + m_q) psi(x)
+ *       - 1/2 sum_mu [ (I - g_mu) U_mu(x) psi(x+mu) + (I + g_mu) U_mu(x-mu)^H psi(x-mu) ]
+ * periodic in all directions, chiral gamma basis with gamma5 = diag(1, 1, -1, -1):
+ *   g1 = [[0,0,0,i],[0,0,i,0],[0,-i,0,0],[-i,0,0,0]]   g2 = [[0,0,0,-1],[0,0,1,0],[0,1,0,0],[-1,0,0,0]]
+ *   g3 = [[0,0,i,0],[0,0,0,-i],[-i,0,0,0],[0,i,0,0]]   g4 = [[0,0,1,0],[0,0,0,1],[1,0,0,0],[0,1,0,0]]
+ *
+ * Vector arguments ("natural layout"): FP64 complex numbers, real then imaginary
+ * part, ordered [rhs][site][spin 0..3][colour 0..2], site = ((t*Lz + z)*Ly + y)*Lx + x.
+ * Gauge: FP64 complex [site][mu 0..3 = x,y,z,t][row][col], U_mu(x) in SU(3).
+ * Vector pointers may be device pointers (any CUDA allocation of this process)
+ * or host pointers (pageable or pinned); the library detects which with
+ * cudaPointerGetAttributes and copies host data through its own device buffers.
+ * All vector buffers stay owned by the caller.  Handles own every device
+ * allocation they make and free it in their destroy call.
+ *
+ * Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ * stream).  Calls return when their results are complete on the host side of
+ * the call (solves synchronise the stream); an op or basis must not be used by
+ * two host threads at once.
+ *
+ * Errors: every call returns an eig_status; 0 is success, >0 a warning, <0 an
+ * error.  Nothing aborts, asserts or traps; eig_last_error() gives the message
+ * of the calling thread's last failure.
+ */
+#ifndef EIGCG_H
+#define EIGCG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    EIG_OK = 0,
+    EIG_NOT_CONVERGED = 1,  /* max_iter reached; x holds the last iterate          */
+    EIG_ERR_ARG = -1,       /* invalid argument (null handle, bad size, bad flag)   */
+    EIG_ERR_OOM = -2,       /* device allocation failed                             */
+    EIG_ERR_BUDGET = -3,    /* request exceeds the handle's capacity                */
+    EIG_ERR_CUDA = -4,      /* CUDA runtime error (message in eig_last_error)       */
+    EIG_ERR_BREAKDOWN = -5, /* CG breakdown: p^H A p <= 0, rho <= 0, NaN or Inf     */
+    EIG_ERR_TIMEOUT = -6    /* a bounded device wait gave up                        */
+} eig_status;
+
+/* Storage precision codes for spinor_prec. */
+#define EIG_PREC_F64 64  /* FP64 storage and arithmetic                                  */
+#define EIG_PREC_F32 32  /* FP32 storage and arithmetic, FP64 reductions                 */
+#define EIG_PREC_F16 16  /* FP16 storage with one FP32 scale per site, FP32 arithmetic   */
+
+typedef struct eig_op_s *eig_op;
+typedef struct eig_basis_s *eig_basis;
+
+typedef struct {
+    int spinor_prec;        /* EIG_PREC_*; storage of Krylov vectors and links           */
+    int link_compress12;    /* 1: store two rows per link, rebuild the third (FP32/F16)  */
+    int max_rhs;            /* largest k of one batched call (1..16); sizes buffers      */
+    double reliable_delta;  /* mixed precision: FP64 residual update when ||r|| falls by
+                               this factor since the last one (0 -> 0.1)                  */
+} eig_op_opts;
+
+typedef struct {
+    int iters;              /* CG iterations (matrix-vector products with A)             */
+    int restarts;           /* eigCG window restarts, or init-CG re-deflations           */
+    int reliable_updates;   /* FP64 residual replacements (mixed precision)              */
+    int converged;          /* 1 if the FP64 true residual met tol                       */
+    double true_rel_res;    /* ||b - A x|| / ||b|| recomputed in FP64                     */
+    double ms;              /* wall time of the call on its stream                       */
+    int n_ritz;             /* Ritz pairs left pending by eigCG                          */
+} eig_stats;
+
+/* Creates the operator A = M^H M for one gauge field and quark mass (Sec. 1).
+ * gauge: host FP64 [V][4][3][3] complex, copied.  dims: Lx, Ly, Lz, Lt, each >= 2
+ * (Lx*Ly*Lz*Lt <= 2^31 / 16).  opts may be NULL (FP64, max_rhs 1).
+ * Errors: EIG_ERR_ARG, EIG_ERR_OOM, EIG_ERR_CUDA. */
+eig_status eig_op_create(const double *gauge, const int dims[4], double m_q, const eig_op_opts *opts,
+                         eig_op *out);
+eig_status eig_op_destroy(eig_op op);
+
+/* out = M in (which 0), M^H in (which 1) or A in (which 2) for k RHS (1..max_rhs),
+ * in the op's storage precision.  in/out: natural layout, may alias.
+ * This is the dslash of the CG matrix-vector product (Fig. 1 step 11). */
+eig_status eig_op_apply(eig_op op, int which, const double *in, double *out, int k, void *stream);
+
+/* Deflation basis U (N x l, l <= max_vecs) with H = U^H A U in FP64 (Sec. 4 box),
+ * stored on the device in the op's window precision (FP64 for F64 ops, else
+ * FP32), plus a pending block of eigCG Ritz vectors.  Bound to one op. */
+eig_status eig_basis_create(eig_op op, int max_vecs, eig_basis *out);
+eig_status eig_basis_destroy(eig_basis basis);
+/* Current number of basis vectors l. */
+eig_status eig_basis_size(eig_basis basis, int *l);
+/* Drops basis vectors beyond the first l (an earlier size); H keeps its leading block. */
+eig_status eig_basis_truncate(eig_basis basis, int l);
+
+/* eigCG(nev, m) of Fig. 1 on one RHS: CG from x (in: initial guess x~0, out:
+ * solution), first deflated with the basis by Eq. 1 when basis is non-NULL and
+ * non-empty (the "init-CG part" of the Sec. 4 box).  Stops when the recursive
+ * ||r|| <= tol ||b||, then checks the FP64 true residual (mixed precision:
+ * reliable updates continue until it meets tol).  On return the nev lowest Ritz
+ * pairs of the final window are pending in the basis (if given).
+ * Requires 1 <= nev, 2*nev < m <= 128.  stats may be NULL. */
+eig_status eig_eigcg_solve(eig_op op, eig_basis basis, const double *b, double *x, int nev, int m, double tol,
+                           int max_iter, eig_stats *stats, void *stream);
+
+/* Sec. 4 box, last three lines: orthonormalises the pending Ritz vectors against U
+ * (classical Gram-Schmidt twice, FP64 accumulation), W = A V-bar in FP64, extends H
+ * with U^H W and V-bar^H W, appends V-bar to U.  Vectors that are numerically in
+ * span(U) are dropped.  EIG_ERR_BUDGET if max_vecs would be exceeded. */
+eig_status eig_basis_grow(eig_basis basis, void *stream);
+
+/* Eq. 1 for k RHS: x0 = x~0 + U H^{-1} U^H (b - A x~0).  x_in may be NULL (x~0 = 0)
+ * and may alias x0. */
+eig_status eig_basis_deflate(eig_basis basis, const double *b, const double *x_in, double *x0, int k,
+                             void *stream);
+
+/* init-CG on k independent RHS (1..max_rhs) batched through one multi-RHS dslash:
+ * Eq. 1 deflation (if basis non-empty), CG, one re-deflation and restart when
+ * ||r||/||b|| first reaches restart_tol (Sec. 5.3; restart_tol <= tol disables it),
+ * FP64 true-residual check.  x: in x~0, out solution.  stats: array of k (or NULL). */
+eig_status eig_initcg_solve(eig_op op, eig_basis basis, const double *b, double *x, double tol, double restart_tol,
+                            int max_iter, int k, eig_stats *stats, void *stream);
+
+/* Rayleigh-Ritz on U (Sec. 5.2): Ritz values (eigenvalues of H, ascending) and
+ * residual norms ||A u - theta u|| (FP64 operator).  evals/resnorms: host arrays of
+ * at least l entries (resnorms may be NULL to skip the residuals); *n = l. */
+eig_status eig_basis_ritz(eig_basis basis, double *evals, double *resnorms, int *n, void *stream);
+
+/* Copies basis vector j (0 <= j < l) to out (natural layout, host or device). */
+eig_status eig_basis_vector(eig_basis basis, int j, double *out, void *stream);
+/* Copies H (l x l, FP64 complex, row-major, host) to out. */
+eig_status eig_basis_h(eig_basis basis, double *out);
+
+/* Kernel instrumentation (diagnostics; the paper reports only per-phase wall
+ * times, Table 1).  Every kernel launch of the library is counted per kernel name
+ * together with its algorithmic bytes (each link, input and output touched
+ * once).  With eig_profile_enable(1) each launch is also bracketed by CUDA
+ * events recorded on the stream it runs on.  eig_profile_read synchronises the
+ * device and returns up to max entries (*n = number of kernel names seen). */
+typedef struct {
+    char name[40];
+    long launches;
+    double ms;      /* summed event time (0 unless timing was enabled) */
+    double bytes;   /* summed algorithmic bytes                         */
+} eig_kernel_stat;
+eig_status eig_profile_enable(int on);
+eig_status eig_profile_reset(void);
+eig_status eig_profile_read(eig_kernel_stat *out, int max, int *n);
+
+/* Message of the calling thread's last error ("" if none). */
+const char *eig_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EIGCG_H */

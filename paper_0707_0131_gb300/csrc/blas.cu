@@ -1,0 +1,345 @@
+// Vector kernels of the CG hot path that are not fused into the stencil:
+// layout conversion at the API boundary, precision conversion for reliable
+// updates, norms, and the p update of Fig. 1 step 9 fused with the eigCG window
+// append of Fig. 1 step 11.13 (V(:, i) = z / sqrt(rho), z = r for P = I).
+// All of them are HBM-bound streaming kernels over the chunk-major field layout.
+#include <cstring>
+
+#include "kernels.cuh"
+#include "prof.h"
+
+namespace eig {
+
+template <typename S>
+struct Calc {
+    using C = typename SpinorStore<S>::C;
+};
+
+static double spb(Prec p) { return p == P64 ? 192.0 : (p == P32 ? 96.0 : 52.0); }
+
+static int stream_grid(long work, int block) {
+    long need = (work + block - 1) / block;
+    long cap = (long)device_sm_count() * 8;
+    if (need > cap) need = cap;
+    return (int)(need < 1 ? 1 : need);
+}
+
+// ---------------------------------------------------------------------------------------
+// natural <-> internal
+// ---------------------------------------------------------------------------------------
+template <typename S>
+__global__ void k_pack(const double2 *__restrict__ nat, FieldView f) {
+    using C = typename SpinorStore<S>::C;
+    const long total = f.V * f.k;
+    for (long g = (long)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += (long)gridDim.x * blockDim.x) {
+        const long s = g / f.k;
+        const int r = (int)(g - s * f.k);
+        const double2 *src = nat + ((long)r * f.V + s) * 12;
+        Spinor<C> v;
+#pragma unroll
+        for (int e = 0; e < 12; e++) {
+            double2 d = src[e];
+            v.s[e / 3][e % 3] = cmk<C>((C)d.x, (C)d.y);
+        }
+        SpinorStore<S>::store(f, s, r, v);
+    }
+}
+
+template <typename S>
+__global__ void k_unpack(FieldView f, double2 *__restrict__ nat) {
+    using C = typename SpinorStore<S>::C;
+    const long total = f.V * f.k;
+    for (long g = (long)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += (long)gridDim.x * blockDim.x) {
+        const long s = g / f.k;
+        const int r = (int)(g - s * f.k);
+        Spinor<C> v;
+        SpinorStore<S>::load(f, s, r, v);
+        double2 *dst = nat + ((long)r * f.V + s) * 12;
+#pragma unroll
+        for (int e = 0; e < 12; e++) dst[e] = make_double2((double)v.s[e / 3][e % 3].re, (double)v.s[e / 3][e % 3].im);
+    }
+}
+
+cudaError_t launch_pack(const double *nat, Field f, cudaStream_t s) {
+    ProfScope prof("pack", (double)f.v.V * f.v.k * (192.0 + spb(f.prec)), s);
+    const int B = 128;
+    const int G = stream_grid(f.v.V * f.v.k, B);
+    const double2 *n = reinterpret_cast<const double2 *>(nat);
+    switch (f.prec) {
+        case P64: k_pack<double><<<G, B, 0, s>>>(n, f.v); break;
+        case P32: k_pack<float><<<G, B, 0, s>>>(n, f.v); break;
+        case P16: k_pack<__half><<<G, B, 0, s>>>(n, f.v); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpack(Field f, double *nat, cudaStream_t s) {
+    ProfScope prof("unpack", (double)f.v.V * f.v.k * (192.0 + spb(f.prec)), s);
+    const int B = 128;
+    const int G = stream_grid(f.v.V * f.v.k, B);
+    double2 *n = reinterpret_cast<double2 *>(nat);
+    switch (f.prec) {
+        case P64: k_unpack<double><<<G, B, 0, s>>>(f.v, n); break;
+        case P32: k_unpack<float><<<G, B, 0, s>>>(f.v, n); break;
+        case P16: k_unpack<__half><<<G, B, 0, s>>>(f.v, n); break;
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------
+// gauge packing: natural [V][4][3][3] complex -> per-direction planes
+// ---------------------------------------------------------------------------------------
+__global__ void k_pack_gauge(const double2 *__restrict__ nat, void *dst, int gformat, long V) {
+    const long total = V * 4;
+    for (long g = (long)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += (long)gridDim.x * blockDim.x) {
+        const long s = g / 4;
+        const int mu = (int)(g - s * 4);
+        const double2 *u = nat + (s * 4 + mu) * 9;
+        if (gformat == GF_F64_18) {
+            double2 *d = static_cast<double2 *>(dst) + (long)mu * 9 * V;
+            for (int e = 0; e < 9; e++) d[(long)e * V + s] = u[e];
+        } else if (gformat == GF_F32_18) {
+            float2 *d = static_cast<float2 *>(dst) + (long)mu * 9 * V;
+            for (int e = 0; e < 9; e++) d[(long)e * V + s] = make_float2((float)u[e].x, (float)u[e].y);
+        } else if (gformat == GF_F32_12) {
+            float4 *d = static_cast<float4 *>(dst) + (long)mu * 3 * V;
+            for (int q = 0; q < 3; q++)
+                d[(long)q * V + s] = make_float4((float)u[2 * q].x, (float)u[2 * q].y, (float)u[2 * q + 1].x,
+                                                 (float)u[2 * q + 1].y);
+        } else {  // GF_F16_12
+            uint2 *d = static_cast<uint2 *>(dst) + (long)mu * 3 * V;
+            for (int q = 0; q < 3; q++) {
+                __half2 h0 = __floats2half2_rn((float)u[2 * q].x, (float)u[2 * q].y);
+                __half2 h1 = __floats2half2_rn((float)u[2 * q + 1].x, (float)u[2 * q + 1].y);
+                d[(long)q * V + s] = make_uint2(*reinterpret_cast<uint32_t *>(&h0), *reinterpret_cast<uint32_t *>(&h1));
+            }
+        }
+    }
+}
+
+cudaError_t launch_pack_gauge(const double *nat, void *dst, int gformat, long V, cudaStream_t s) {
+    ProfScope prof("pack_gauge", (double)V * 4 * 288.0, s);
+    const int B = 128;
+    k_pack_gauge<<<stream_grid(V * 4, B), B, 0, s>>>(reinterpret_cast<const double2 *>(nat), dst, gformat, V);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------
+// out = ca * a + cb * b
+// ---------------------------------------------------------------------------------------
+template <typename A, typename B>
+struct Wider {
+    using T = float;
+};
+template <typename B>
+struct Wider<double, B> {
+    using T = double;
+};
+template <typename A>
+struct Wider<A, double> {
+    using T = double;
+};
+template <>
+struct Wider<double, double> {
+    using T = double;
+};
+
+template <typename SO, typename SA, typename SB>
+__global__ void k_combine(FieldView o, double ca, FieldView a, double cb, FieldView b, int has_b) {
+    using C = typename Wider<typename Wider<SO, SA>::T, SB>::T;
+    using CO = typename SpinorStore<SO>::C;
+    using CA = typename SpinorStore<SA>::C;
+    using CB = typename SpinorStore<SB>::C;
+    const long total = o.V * o.k;
+    const C fa = (C)ca, fb = (C)cb;
+    for (long g = (long)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += (long)gridDim.x * blockDim.x) {
+        const long s = g / o.k;
+        const int r = (int)(g - s * o.k);
+        Spinor<CA> va;
+        SpinorStore<SA>::load(a, s, r, va);
+        Spinor<CB> vb;
+        if (has_b) SpinorStore<SB>::load(b, s, r, vb);
+        Spinor<CO> vo;
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                C re = fa * (C)va.s[i][j].re, im = fa * (C)va.s[i][j].im;
+                if (has_b) {
+                    re += fb * (C)vb.s[i][j].re;
+                    im += fb * (C)vb.s[i][j].im;
+                }
+                vo.s[i][j] = cmk<CO>((CO)re, (CO)im);
+            }
+        SpinorStore<SO>::store(o, s, r, vo);
+    }
+}
+
+template <typename SO, typename SA>
+static void combine_b(Field o, double ca, Field a, double cb, Field b, int G, int B, cudaStream_t s) {
+    const int hb = b.v.data != nullptr;
+    Prec pb = hb ? b.prec : a.prec;
+    switch (pb) {
+        case P64: k_combine<SO, SA, double><<<G, B, 0, s>>>(o.v, ca, a.v, cb, b.v, hb); break;
+        case P32: k_combine<SO, SA, float><<<G, B, 0, s>>>(o.v, ca, a.v, cb, b.v, hb); break;
+        case P16: k_combine<SO, SA, __half><<<G, B, 0, s>>>(o.v, ca, a.v, cb, b.v, hb); break;
+    }
+}
+
+template <typename SO>
+static void combine_a(Field o, double ca, Field a, double cb, Field b, int G, int B, cudaStream_t s) {
+    switch (a.prec) {
+        case P64: combine_b<SO, double>(o, ca, a, cb, b, G, B, s); break;
+        case P32: combine_b<SO, float>(o, ca, a, cb, b, G, B, s); break;
+        case P16: combine_b<SO, __half>(o, ca, a, cb, b, G, B, s); break;
+    }
+}
+
+cudaError_t launch_combine(Field out, double ca, Field a, double cb, Field b, cudaStream_t s) {
+    ProfScope prof("combine",
+                   (double)out.v.V * out.v.k * (spb(out.prec) + spb(a.prec) + (b.v.data ? spb(b.prec) : 0.0)), s);
+    const int B = 128;
+    const int G = stream_grid(out.v.V * out.v.k, B);
+    switch (out.prec) {
+        case P64: combine_a<double>(out, ca, a, cb, b, G, B, s); break;
+        case P32: combine_a<float>(out, ca, a, cb, b, G, B, s); break;
+        case P16: combine_a<__half>(out, ca, a, cb, b, G, B, s); break;
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------
+// norms
+// ---------------------------------------------------------------------------------------
+template <typename S>
+__global__ void __launch_bounds__(256) k_norm2(FieldView f, CGScalars *st, int as_rho, double *h_rho, int iter,
+                                               double *partials, unsigned *counter) {
+    using C = typename SpinorStore<S>::C;
+    __shared__ double smem[(256 / 32) * MAX_RHS];
+    const long total = f.V * f.k;
+    double n = 0.0;
+    for (long g = (long)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += (long)gridDim.x * blockDim.x) {
+        const long s = g / f.k;
+        const int r = (int)(g - s * f.k);
+        Spinor<C> v;
+        SpinorStore<S>::load(f, s, r, v);
+        C a = 0;
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) a += v.s[i][j].re * v.s[i][j].re + v.s[i][j].im * v.s[i][j].im;
+        n += (double)a;
+    }
+    const double bs = block_reduce_rhs(n, f.k, smem);
+    const int k = f.k;
+    grid_reduce_rhs(bs, k, partials, counter, smem, [=](int r, double tot) {
+        st[r].aux = tot;
+        if (as_rho) {
+            st[r].rho = tot;
+            st[r].rho_prev = tot;
+            if (h_rho) h_rho[(long)iter * k + r] = tot;
+        }
+    });
+}
+
+cudaError_t launch_norm2(Field f, CGScalars *st, bool as_rho, History h, int iter, RedScratch red, cudaStream_t s) {
+    ProfScope prof("norm2", (double)f.v.V * f.v.k * spb(f.prec), s);
+    const int B = 256;
+    int G = stream_grid(f.v.V * f.v.k, B);
+    if (G > red.max_blocks) G = red.max_blocks;
+    switch (f.prec) {
+        case P64: k_norm2<double><<<G, B, 0, s>>>(f.v, st, as_rho, h.rho, iter, red.partials, red.counter); break;
+        case P32: k_norm2<float><<<G, B, 0, s>>>(f.v, st, as_rho, h.rho, iter, red.partials, red.counter); break;
+        case P16: k_norm2<__half><<<G, B, 0, s>>>(f.v, st, as_rho, h.rho, iter, red.partials, red.counter); break;
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------
+// p = r + beta p  (+ window append v = r / sqrt(rho))
+// ---------------------------------------------------------------------------------------
+template <typename S, typename SV>
+__global__ void k_pupdate(FieldView r, FieldView p, int first, const CGScalars *st, FieldView v, int append) {
+    using C = typename SpinorStore<S>::C;
+    using CV = typename SpinorStore<SV>::C;
+    {
+        bool any = false;
+        for (int q = 0; q < r.k; q++) any = any || st[q].active;
+        if (!any) return;
+    }
+    const long total = r.V * r.k;
+    for (long g = (long)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += (long)gridDim.x * blockDim.x) {
+        const long s = g / r.k;
+        const int q = (int)(g - s * r.k);
+        Spinor<C> rr, pp;
+        SpinorStore<S>::load(r, s, q, rr);
+        const CGScalars &sc = st[q];
+        if (first) {
+            pp = rr;
+        } else {
+            const C be = sc.active ? (C)sc.beta : (C)0;
+            SpinorStore<S>::load(p, s, q, pp);
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+#pragma unroll
+                for (int j = 0; j < 3; j++)
+                    pp.s[i][j] = cmk<C>(rr.s[i][j].re + be * pp.s[i][j].re, rr.s[i][j].im + be * pp.s[i][j].im);
+        }
+        SpinorStore<S>::store(p, s, q, pp);
+        if (append && sc.active) {
+            const CV sc_inv = (CV)(1.0 / sqrt(sc.rho));
+            Spinor<CV> vv;
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+#pragma unroll
+                for (int j = 0; j < 3; j++) vv.s[i][j] = cmk<CV>((CV)rr.s[i][j].re * sc_inv, (CV)rr.s[i][j].im * sc_inv);
+            SpinorStore<SV>::store(v, s, q, vv);
+        }
+    }
+}
+
+cudaError_t launch_pupdate(Field r, Field p, bool first, CGScalars *st, Field v_append, cudaStream_t s) {
+    ProfScope prof("pupdate", (double)r.v.V * r.v.k * ((first ? 2.0 : 3.0) * spb(r.prec)) +
+                                  (v_append.v.data ? (double)r.v.V * spb(v_append.prec) : 0.0), s);
+    const int B = 128;
+    const int G = stream_grid(r.v.V * r.v.k, B);
+    const int app = v_append.v.data != nullptr;
+    if (app && v_append.prec == P16) return cudaErrorInvalidValue;
+    const bool v64 = app && v_append.prec == P64;
+    switch (r.prec) {
+        case P64:
+            if (app && !v64) return cudaErrorInvalidValue;
+            k_pupdate<double, double><<<G, B, 0, s>>>(r.v, p.v, first, st, v_append.v, app);
+            break;
+        case P32:
+            if (v64) return cudaErrorInvalidValue;
+            k_pupdate<float, float><<<G, B, 0, s>>>(r.v, p.v, first, st, v_append.v, app);
+            break;
+        case P16:
+            if (v64) return cudaErrorInvalidValue;
+            k_pupdate<__half, float><<<G, B, 0, s>>>(r.v, p.v, first, st, v_append.v, app);
+            break;
+    }
+    return cudaGetLastError();
+}
+
+__global__ void k_cg_init(CGScalars *st, int k, double tol2, double *h_beta) {
+    const int r = threadIdx.x;
+    if (r >= k) return;
+    st[r].target = tol2 * st[r].aux;
+    st[r].active = 1;
+    st[r].breakdown = 0;
+    st[r].alpha = 0.0;
+    st[r].beta = 0.0;
+    st[r].pAp = 0.0;
+    st[r].iters = 0;
+    if (h_beta) h_beta[k + r] = 0.0;  // beta_1 := 0
+}
+
+cudaError_t launch_cg_init(CGScalars *st, int k, double tol, History h, cudaStream_t s) {
+    ProfScope prof("cg_init", 0.0, s);
+    k_cg_init<<<1, 32, 0, s>>>(st, k, tol * tol, h.beta);
+    return cudaGetLastError();
+}
+
+}  // namespace eig

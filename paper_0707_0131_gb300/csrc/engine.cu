@@ -1,0 +1,1253 @@
+// Solver engine behind the C ABI of include/eigcg.h.
+//
+// Flow of one CG iteration j (Fig. 1, P = I), all on the caller's stream with the
+// scalars alpha, beta, rho resident on the device:
+//   k_pupdate          p = r + beta_j p        (+ eigCG step 11.13: V(:, i) = r / sqrt(rho))
+//   k_dslash<NORM>     u = M p, pAp = ||u||^2, alpha_j = rho / pAp         (steps 11-12)
+//   k_dslash<CG>       t = M^H u, x += alpha p, r -= alpha t, rho, beta_{j+1}  (steps 13-14, 4, 8)
+// The host synchronises only every CHECK iterations (convergence, reliable
+// updates) and at eigCG restarts, where it reads the alpha/beta history, forms the
+// window projection T (Eq. 4 plus the restarted head), solves the small FP64
+// eigenproblems of steps 11.3-11.6 and launches the in-place restart GEMM of step
+// 11.7 with the step-11.8 row fused in.
+//
+// Mixed precision: Krylov vectors live in FP32 or FP16 storage; x accumulates in
+// FP32 between reliable updates, which add it into an FP64 solution and replace r
+// by the FP64 true residual b - A x when ||r|| has fallen by reliable_delta.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "dense.h"
+#include "eigcg.h"
+#include "kernels.cuh"
+#include "prof.h"
+
+namespace eig {
+
+using cd = std::complex<double>;
+
+struct Error {
+    eig_status st;
+    std::string msg;
+};
+
+static thread_local std::string g_last_error;
+
+#define CUDA_CK(call)                                                                           \
+    do {                                                                                        \
+        cudaError_t e_ = (call);                                                                \
+        if (e_ != cudaSuccess) throw Error{EIG_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)}; \
+    } while (0)
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t n = 0;
+    void alloc(size_t bytes) {
+        release();
+        if (bytes == 0) return;
+        cudaError_t e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            cudaGetLastError();
+            throw Error{EIG_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed"};
+        }
+        n = bytes;
+    }
+    void ensure(size_t bytes) {
+        if (bytes > n) alloc(bytes);
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    ~DevBuf() { release(); }
+    template <typename T>
+    T *as() const {
+        return static_cast<T *>(p);
+    }
+};
+
+struct PinBuf {
+    void *p = nullptr;
+    size_t n = 0;
+    void ensure(size_t bytes) {
+        if (bytes <= n) return;
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        n = 0;
+        if (cudaMallocHost(&p, bytes) != cudaSuccess) {
+            p = nullptr;
+            cudaGetLastError();
+            throw Error{EIG_ERR_OOM, "cudaMallocHost failed"};
+        }
+        n = bytes;
+    }
+    ~PinBuf() {
+        if (p) cudaFreeHost(p);
+    }
+    template <typename T>
+    T *as() const {
+        return static_cast<T *>(p);
+    }
+};
+
+// A field buffer able to hold up to kcap RHS.
+struct FieldBuf {
+    Prec prec = P64;
+    long V = 0;
+    int kcap = 0;
+    DevBuf data, scale;
+    void alloc(Prec p, long v, int k) {
+        prec = p;
+        V = v;
+        kcap = k;
+        data.alloc(field_bytes(p, v, k));
+        if (p == P16) scale.alloc((size_t)v * k * sizeof(float));
+    }
+    Field view(int k) const {
+        Field f;
+        f.prec = prec;
+        f.v.data = data.p;
+        f.v.scale = scale.as<float>();
+        f.v.V = V;
+        f.v.k = k;
+        return f;
+    }
+};
+
+static Field null_field() {
+    Field f;
+    memset(&f, 0, sizeof(f));
+    return f;
+}
+
+static Field field_at(Prec p, void *data, long V, int k) {
+    Field f;
+    f.prec = p;
+    f.v.data = data;
+    f.v.scale = nullptr;
+    f.v.V = V;
+    f.v.k = k;
+    return f;
+}
+
+constexpr int CHECK = 16;        // iterations between host checks
+constexpr int MAX_WINDOW = 128;  // largest eigCG m
+constexpr int MAX_NEV = 16;
+constexpr int RED_BLOCKS = 2048;
+
+}  // namespace eig
+
+using namespace eig;
+
+struct eig_op_s {
+    int L[4];
+    long V;
+    double m_q;
+    Prec prec;     // Krylov storage
+    Prec wprec;    // window / basis / x_lo storage (P64 or P32)
+    int gf_inner;
+    int max_rhs;
+    double delta;
+    DevBuf gauge64, gauge_in;
+    // workspace
+    FieldBuf r, p, u, xlo, b64, x64, r64, u64, rsv, xsv;
+    DevBuf nat_in, nat_out;
+    DevBuf st;
+    PinBuf st_h;
+    DevBuf hist;
+    int hist_cap = 0;
+    PinBuf hist_h;
+    DevBuf red_partials, red_counter;
+    // eigCG window
+    DevBuf win, tprev, tcur, col_off, qz, wv;
+    int win_slots = 0;
+    std::mutex mu;
+
+    long ncomplex() const { return V * 12; }
+    size_t wfield_bytes() const { return field_bytes(wprec, V, 1); }
+    RedScratch red() const {
+        RedScratch r;
+        r.partials = red_partials.as<double>();
+        r.counter = red_counter.as<unsigned>();
+        r.max_blocks = RED_BLOCKS;
+        return r;
+    }
+    DslashCall call(Field in, Field out, bool dag, bool f64) const {
+        DslashCall c;
+        c.in = in;
+        c.out = out;
+        c.gauge.data = f64 ? gauge64.p : gauge_in.p;
+        c.gauge.V = V;
+        c.gformat = f64 ? GF_F64_18 : gf_inner;
+        for (int i = 0; i < 4; i++) c.L[i] = L[i];
+        c.V = V;
+        c.k = in.v.k;
+        c.diag = 4.0 + m_q;
+        c.dagger = dag;
+        return c;
+    }
+    History history(int k) const {
+        History h;
+        h.alpha = hist.as<double>();
+        h.beta = h.alpha + (size_t)hist_cap * k;
+        h.rho = h.beta + (size_t)hist_cap * k;
+        h.cap = hist_cap;
+        return h;
+    }
+    void ensure_history(int iters, int k) {
+        const int need = iters + 4;
+        if (need * k > hist_cap * k || hist_cap < need) {
+            hist.alloc((size_t)need * k * 3 * sizeof(double));
+            hist_cap = need;
+        }
+        hist_h.ensure((size_t)hist_cap * k * 3 * sizeof(double));
+    }
+};
+
+struct eig_basis_s {
+    eig_op_s *op;
+    int max_vecs;
+    int l = 0;
+    DevBuf U;        // max_vecs window-precision fields
+    DevBuf pend;     // MAX_NEV pending Ritz vectors
+    DevBuf W;        // MAX_NEV scratch fields
+    int npend = 0;
+    std::vector<double> pend_ritz;
+    std::vector<cd> H, Lc;  // H = U^H A U and its Cholesky factor (row-major l x l)
+    bool chol_ok = true;
+    DevBuf C, Y;            // device small matrices
+    PinBuf Ch;
+    std::mutex mu;
+    long fsize() const { return op->V * 12; }  // complex entries per field
+};
+
+namespace eig {
+
+static void set_error(const Error &e) { g_last_error = e.msg; }
+
+static bool is_device_ptr(const void *p) {
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static void sync(cudaStream_t s) { CUDA_CK(cudaStreamSynchronize(s)); }
+
+// Sets a field to zero without reading it (fresh allocations may hold NaN patterns).
+static void zero_field(Field f, cudaStream_t s) {
+    CUDA_CK(cudaMemsetAsync(f.v.data, 0, field_bytes(f.prec, f.v.V, f.v.k), s));
+    if (f.prec == P16 && f.v.scale) CUDA_CK(cudaMemsetAsync(f.v.scale, 0, (size_t)f.v.V * f.v.k * sizeof(float), s));
+}
+
+// ------------------------------------------------------------------------------------
+// building blocks on an op
+// ------------------------------------------------------------------------------------
+static void apply_M(eig_op_s *op, Field in, Field out, bool dag, bool f64, cudaStream_t s) {
+    CUDA_CK(launch_dslash(op->call(in, out, dag, f64), s));
+}
+
+// out = A in in FP64 (uses op->u64 as scratch; in/out must not be u64)
+static void apply_A64(eig_op_s *op, Field in, Field out, cudaStream_t s) {
+    Field u = op->u64.view(in.v.k);
+    apply_M(op, in, u, false, true, s);
+    apply_M(op, u, out, true, true, s);
+}
+
+// natural (host or device) -> internal FP64 field
+static void load_natural(eig_op_s *op, const double *nat, Field dst, cudaStream_t s) {
+    const size_t bytes = (size_t)op->V * 12 * 16 * dst.v.k;
+    const double *src = nat;
+    if (!is_device_ptr(nat)) {
+        CUDA_CK(cudaMemcpyAsync(op->nat_in.p, nat, bytes, cudaMemcpyHostToDevice, s));
+        src = op->nat_in.as<double>();
+    }
+    CUDA_CK(launch_pack(src, dst, s));
+}
+
+static void store_natural(eig_op_s *op, Field src, double *nat, cudaStream_t s) {
+    const size_t bytes = (size_t)op->V * 12 * 16 * src.v.k;
+    if (is_device_ptr(nat)) {
+        CUDA_CK(launch_unpack(src, nat, s));
+    } else {
+        CUDA_CK(launch_unpack(src, op->nat_out.as<double>(), s));
+        CUDA_CK(cudaMemcpyAsync(nat, op->nat_out.p, bytes, cudaMemcpyDeviceToHost, s));
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// eigCG window state (Fig. 1 right box), host bookkeeping of device slots
+// ------------------------------------------------------------------------------------
+struct Window {
+    int nev, m;
+    int i = 0;               // vectors in the window
+    int kh = 0;              // size of the restarted Ritz head
+    int j0 = 1;              // iteration whose z sits at window index kh
+    std::vector<double> Mh;  // head Ritz values
+    std::vector<cd> trow;    // w^H V_new of the last restart (unnormalised)
+    std::vector<int> slots;  // physical slot of window index
+    std::vector<int> freel;  // free slots
+    int restarts = 0;
+    int save_prev_at = -1;   // iteration whose t goes to t_prev
+    bool tprev_is_a = true;  // which buffer currently holds t_prev
+};
+
+// Builds T (n x n) of the current window from the device history (host copy).
+static void window_T(const Window &w, int n, const double *ha, const double *hb, const double *hr,
+                     std::vector<cd> &T) {
+    T.assign((size_t)n * n, cd(0.0));
+    for (int a = 0; a < w.kh && a < n; a++) T[(size_t)a * n + a] = w.Mh[a];
+    if (w.kh > 0 && w.kh < n) {
+        const double sr = std::sqrt(hr[w.j0 - 1]);
+        for (int a = 0; a < w.kh; a++) {
+            const cd v = w.trow[a] / sr;
+            T[(size_t)w.kh * n + a] = v;
+            T[(size_t)a * n + w.kh] = std::conj(v);
+        }
+    }
+    for (int q = 0; w.kh + q < n; q++) {
+        const int jj = w.j0 + q;
+        const int ix = w.kh + q;
+        T[(size_t)ix * n + ix] = 1.0 / ha[jj] + (jj > 1 ? hb[jj] / ha[jj - 1] : 0.0);
+        if (q >= 1) {
+            const double off = -std::sqrt(hb[jj]) / ha[jj - 1];
+            T[(size_t)ix * n + ix - 1] = off;
+            T[(size_t)(ix - 1) * n + ix] = off;
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// CG driver (single or batched)
+// ------------------------------------------------------------------------------------
+struct Solve {
+    eig_op_s *op;
+    cudaStream_t s;
+    int k;
+    bool mixed;
+    Field b64, x64, r64, u64, r, p, u, xlo;
+    History h;
+    RedScratch red;
+    CGScalars *st;
+    CGScalars *sth;
+    std::vector<int> reliable;  // per RHS
+    std::vector<double> rmax;   // max ||r|| since last reliable update
+    int j = 0;                  // last issued iteration
+    int j_checked = 0;          // history read up to here
+    double tol;
+
+    void read_scalars() {
+        CUDA_CK(cudaMemcpyAsync(sth, st, sizeof(CGScalars) * k, cudaMemcpyDeviceToHost, s));
+        sync(s);
+    }
+    void write_scalars() { CUDA_CK(cudaMemcpyAsync(st, sth, sizeof(CGScalars) * k, cudaMemcpyHostToDevice, s)); }
+    void read_history(int upto) {
+        double *hh = op->hist_h.as<double>();
+        const size_t n = (size_t)(upto + 2) * k;
+        CUDA_CK(cudaMemcpyAsync(hh, h.alpha, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CUDA_CK(cudaMemcpyAsync(hh + (size_t)h.cap * k, h.beta, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CUDA_CK(cudaMemcpyAsync(hh + 2 * (size_t)h.cap * k, h.rho, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+        sync(s);
+    }
+    const double *ha() const { return op->hist_h.as<double>(); }
+    const double *hb() const { return op->hist_h.as<double>() + (size_t)h.cap * k; }
+    const double *hr() const { return op->hist_h.as<double>() + 2 * (size_t)h.cap * k; }
+
+    // r64 = b - A x64 (FP64); with set_rho the CG scalars take the true residual.
+    void true_residual(bool set_rho) {
+        if (mixed) {
+            CUDA_CK(launch_combine(x64, 1.0, x64, 1.0, xlo, s));
+            zero_field(xlo, s);
+        }
+        apply_M(op, x64, u64, false, true, s);
+        CUDA_CK(launch_dslash_resid(op->call(u64, r64, true, true), b64, r64, st, h, j, set_rho, red, s));
+        if (mixed && set_rho) CUDA_CK(launch_combine(r, 1.0, r64, 0.0, null_field(), s));
+    }
+
+    // Sets up r, rho, target from b64 and the initial guess in x64.
+    void start(double tol_) {
+        tol = tol_;
+        CUDA_CK(launch_norm2(b64, st, false, h, 0, red, s));
+        CUDA_CK(launch_cg_init(st, k, tol, h, s));
+        if (mixed) zero_field(xlo, s);
+        true_residual(false);
+        if (mixed) CUDA_CK(launch_combine(r, 1.0, r64, 0.0, null_field(), s));
+        CUDA_CK(launch_norm2(r64, st, true, h, 0, red, s));
+        read_scalars();
+        for (int q = 0; q < k; q++) {
+            sth[q].iters = 0;
+            if (!(sth[q].aux > sth[q].target)) sth[q].active = 0;
+            if (!std::isfinite(sth[q].aux)) {
+                sth[q].active = 0;
+                sth[q].breakdown = 1;
+            }
+        }
+        write_scalars();
+        j = 0;
+        j_checked = 0;
+        rmax.assign(k, 0.0);
+        for (int q = 0; q < k; q++) rmax[q] = std::sqrt(sth[q].aux);
+        reliable.assign(k, 0);
+    }
+
+    // Reliable-update test on the history since the last check (host has read it).
+    bool needs_reliable() {
+        if (!mixed) return false;
+        bool trig = false;
+        const double *r_ = hr();
+        for (int q = 0; q < k; q++) {
+            if (!sth[q].active) continue;
+            for (int jj = j_checked + 1; jj <= j; jj++) {
+                const double rn = std::sqrt(r_[(size_t)jj * k + q]);
+                if (rn > rmax[q]) rmax[q] = rn;
+            }
+            const double cur = std::sqrt(r_[(size_t)j * k + q]);
+            if (cur < op->delta * rmax[q]) trig = true;
+        }
+        return trig;
+    }
+    void reliable_update() {
+        true_residual(true);
+        read_scalars();
+        for (int q = 0; q < k; q++) {
+            rmax[q] = std::sqrt(sth[q].rho);
+            reliable[q]++;
+        }
+    }
+};
+
+static void check_breakdown(const Solve &sv) {
+    for (int q = 0; q < sv.k; q++)
+        if (sv.sth[q].breakdown) throw Error{EIG_ERR_BREAKDOWN, "CG breakdown (p^H A p <= 0, NaN or Inf)"};
+}
+
+// Runs CG iterations until every RHS is inactive or max_iter.  With a window,
+// performs the eigCG additions.  Returns false if max_iter was hit.
+static bool cg_run(Solve &sv, int max_iter, Window *w, eig_op_s *op) {
+    cudaStream_t s = sv.s;
+    const int k = sv.k;
+    int since = CHECK;  // force a check at the start
+    while (true) {
+        const bool restart_now = w && w->i == w->m;
+        if (since >= CHECK || restart_now || sv.j >= max_iter) {
+            sv.read_scalars();
+            bool any = false;
+            for (int q = 0; q < k; q++) any = any || sv.sth[q].active;
+            if (w && !any && sv.sth[0].iters < sv.j) {
+                // speculative iterations after convergence appended nothing
+                const int skipped = sv.j - sv.sth[0].iters;
+                for (int t = 0; t < skipped; t++) {
+                    w->freel.push_back(w->slots.back());
+                    w->slots.pop_back();
+                    w->i--;
+                }
+                sv.j = sv.sth[0].iters;
+            }
+            if (!any) break;
+            if (sv.j >= max_iter) return false;
+            sv.read_history(sv.j);
+            if (sv.needs_reliable()) {
+                sv.reliable_update();
+                check_breakdown(sv);
+            }
+            sv.j_checked = sv.j;
+            since = 0;
+        }
+        const int j = ++sv.j;
+        since++;
+        Field vapp = null_field();
+        int slot = -1;
+        std::vector<cd> QZ;
+        std::vector<double> Mnew;
+        int nout = 0;
+        if (w) {
+            if (restart_now) {
+                // Fig. 1 steps 11.3-11.6 on the host from T_m
+                std::vector<cd> T;
+                window_T(*w, w->m, sv.ha(), sv.hb(), sv.hr(), T);
+                QZ.resize((size_t)w->m * 2 * w->nev);
+                Mnew.resize(2 * w->nev);
+                nout = dense::restart_coefficients(w->m, T.data(), w->kh, w->nev,
+                                                   std::max(w->m, 2 * w->nev) * 2.2e-16, QZ.data(), Mnew.data());
+                if (nout < 1) throw Error{EIG_ERR_BREAKDOWN, "eigCG restart basis is empty"};
+                slot = w->freel.back();  // the spare slot
+            } else {
+                slot = w->freel.back();
+            }
+            w->freel.pop_back();
+            vapp = field_at(op->wprec, (char *)op->win.p + (size_t)slot * op->wfield_bytes(), op->V, 1);
+        }
+        CUDA_CK(launch_pupdate(sv.r, sv.p, j == 1, sv.st, vapp, s));
+        CUDA_CK(launch_dslash_norm(op->call(sv.p, sv.u, false, op->prec == P64),
+                                   sv.st, sv.h, j, sv.red, s));
+        Field tsave = null_field();
+        if (w) {
+            const bool becomes_full = !restart_now && (w->i + 1 == w->m);
+            void *tp = w->tprev_is_a ? op->tprev.p : op->tcur.p;
+            void *tc = w->tprev_is_a ? op->tcur.p : op->tprev.p;
+            if (restart_now) tsave = field_at(op->wprec, tc, op->V, 1);
+            else if (becomes_full) tsave = field_at(op->wprec, tp, op->V, 1);
+        }
+        CUDA_CK(launch_dslash_cg(op->call(sv.u, sv.u, true, op->prec == P64), sv.p, sv.xlo, sv.r, tsave, sv.st, sv.h,
+                                 j, sv.red, s));
+        if (w) {
+            if (restart_now) {
+                // step 11.7 (V <- V QZ in place) fused with step 11.8 (w^H V)
+                const int m = w->m;
+                std::vector<long> off(m);
+                const long fs = (long)op->V * 12;
+                for (int a = 0; a < m; a++) off[a] = (long)w->slots[a] * fs;
+                CUDA_CK(cudaMemcpyAsync(op->col_off.p, off.data(), m * sizeof(long), cudaMemcpyHostToDevice, s));
+                std::vector<double> qz((size_t)m * nout * 2);
+                for (int a = 0; a < m; a++)
+                    for (int c = 0; c < nout; c++) {
+                        qz[((size_t)a * nout + c) * 2] = QZ[(size_t)c * m + a].real();
+                        qz[((size_t)a * nout + c) * 2 + 1] = QZ[(size_t)c * m + a].imag();
+                    }
+                CUDA_CK(cudaMemcpyAsync(op->qz.p, qz.data(), qz.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+                ColSet Vw;
+                Vw.base = op->win.p;
+                Vw.f64 = op->wprec == P64;
+                Vw.ki = 1;
+                Vw.col_stride = 0;
+                Vw.ncols = m;
+                Vw.col_off = op->col_off.as<long>();
+                void *tp = w->tprev_is_a ? op->tprev.p : op->tcur.p;
+                void *tc = w->tprev_is_a ? op->tcur.p : op->tprev.p;
+                CUDA_CK(launch_window_restart(Vw, m, op->qz.as<double>(), nout, tc, tp, sv.h.beta + (size_t)j * k,
+                                              op->ncomplex(), op->wv.as<double>(), sv.red, s));
+                // the restart reads qz/col_off asynchronously: keep host vectors alive until done
+                sync(s);
+                std::vector<double> wv(2 * nout);
+                CUDA_CK(cudaMemcpy(wv.data(), op->wv.p, wv.size() * sizeof(double), cudaMemcpyDeviceToHost));
+                std::vector<int> newslots(w->slots.begin(), w->slots.begin() + nout);
+                for (int a = nout; a < m; a++) w->freel.push_back(w->slots[a]);
+                newslots.push_back(slot);
+                w->slots = newslots;
+                w->kh = nout;
+                w->Mh.assign(Mnew.begin(), Mnew.begin() + nout);
+                w->trow.resize(nout);
+                for (int c = 0; c < nout; c++) w->trow[c] = cd(wv[2 * c], wv[2 * c + 1]);
+                w->j0 = j;
+                w->i = nout + 1;
+                w->restarts++;
+                if (w->i == w->m) w->tprev_is_a = !w->tprev_is_a;  // this t is the next t_prev
+            } else {
+                w->slots.push_back(slot);
+                w->i++;
+            }
+        }
+    }
+    check_breakdown(sv);
+    return true;
+}
+
+// Final FP64 residual; re-activates RHS that missed tol (up to a few times).
+static bool cg_finish(Solve &sv, int max_iter, Window *w, eig_op_s *op, int &extra_rounds) {
+    sv.true_residual(true);
+    sv.read_scalars();
+    bool again = false;
+    for (int q = 0; q < sv.k; q++) {
+        const double bn2 = sv.sth[q].target / (sv.tol * sv.tol);
+        const bool ok = sv.sth[q].aux <= sv.tol * sv.tol * bn2 * (1.0 + 1e-12) || bn2 == 0.0;
+        if (!ok && !sv.sth[q].breakdown && sv.j < max_iter && extra_rounds < 8) {
+            sv.sth[q].active = 1;
+            again = true;
+        }
+    }
+    if (again) {
+        extra_rounds++;
+        sv.write_scalars();
+        for (int q = 0; q < sv.k; q++) sv.rmax[q] = std::sqrt(sv.sth[q].aux);
+    }
+    (void)w;
+    (void)op;
+    return again;
+}
+
+static Solve make_solve(eig_op_s *op, int k, cudaStream_t s, int max_iter) {
+    Solve sv;
+    sv.op = op;
+    sv.s = s;
+    sv.k = k;
+    sv.mixed = op->prec != P64;
+    sv.b64 = op->b64.view(k);
+    sv.x64 = op->x64.view(k);
+    sv.u64 = op->u64.view(k);
+    sv.p = op->p.view(k);
+    sv.u = op->u.view(k);
+    if (sv.mixed) {
+        sv.r64 = op->r64.view(k);
+        sv.r = op->r.view(k);
+        sv.xlo = op->xlo.view(k);
+    } else {
+        sv.r64 = op->r.view(k);
+        sv.r = sv.r64;
+        sv.xlo = sv.x64;
+    }
+    op->ensure_history(max_iter + 2, k);
+    sv.h = op->history(k);
+    sv.red = op->red();
+    sv.st = op->st.as<CGScalars>();
+    sv.sth = op->st_h.as<CGScalars>();
+    return sv;
+}
+
+// ------------------------------------------------------------------------------------
+// basis operations
+// ------------------------------------------------------------------------------------
+static ColSet basis_cols(eig_basis_s *B, int first, int n) {
+    ColSet c;
+    c.base = (char *)B->U.p + (size_t)first * B->op->wfield_bytes();
+    c.f64 = B->op->wprec == P64;
+    c.ki = 1;
+    c.col_stride = B->fsize();
+    c.ncols = n;
+    c.col_off = nullptr;
+    return c;
+}
+
+static ColSet field_cols(void *base, bool f64, int k, long fsize, int ncols, bool rhs_inner) {
+    ColSet c;
+    c.base = base;
+    c.f64 = f64;
+    c.ki = rhs_inner ? k : 1;
+    c.col_stride = rhs_inner ? 0 : fsize;
+    c.ncols = ncols;
+    c.col_off = nullptr;
+    return c;
+}
+
+static void refactor(eig_basis_s *B) {
+    const int l = B->l;
+    B->Lc = B->H;
+    B->chol_ok = l == 0 || dense::cholesky(l, B->Lc.data());
+}
+
+// x64 <- x64 + U H^{-1} U^H r64 for k RHS (r64 given in FP64).
+static void deflate_into(eig_basis_s *B, Field r64, Field x64, cudaStream_t s) {
+    eig_op_s *op = B->op;
+    const int l = B->l, k = r64.v.k;
+    if (l == 0) return;
+    if (!B->chol_ok) throw Error{EIG_ERR_BREAKDOWN, "H = U^H A U is not positive definite"};
+    Field rsv = op->rsv.view(k);
+    CUDA_CK(launch_combine(rsv, 1.0, r64, 0.0, null_field(), s));
+    const bool f64 = op->wprec == P64;
+    ColSet R = field_cols(rsv.v.data, f64, k, B->fsize(), k, true);
+    B->C.ensure((size_t)l * k * 16);
+    CUDA_CK(launch_gemm_ahb(basis_cols(B, 0, l), R, op->ncomplex(), B->C.as<double>(), op->red(), s));
+    B->Ch.ensure((size_t)l * k * 16);
+    CUDA_CK(cudaMemcpyAsync(B->Ch.p, B->C.p, (size_t)l * k * 16, cudaMemcpyDeviceToHost, s));
+    sync(s);
+    // solve H y = c per RHS (C is l x k row-major)
+    std::vector<cd> Yc((size_t)l * k);
+    const cd *Cc = B->Ch.as<cd>();
+    for (int a = 0; a < l; a++)
+        for (int q = 0; q < k; q++) Yc[(size_t)q * l + a] = Cc[(size_t)a * k + q];
+    dense::chol_solve(l, B->Lc.data(), Yc.data(), k);
+    std::vector<cd> Yr((size_t)l * k);
+    for (int a = 0; a < l; a++)
+        for (int q = 0; q < k; q++) Yr[(size_t)a * k + q] = Yc[(size_t)q * l + a];
+    B->Y.ensure((size_t)l * k * 16);
+    CUDA_CK(cudaMemcpyAsync(B->Y.p, Yr.data(), Yr.size() * 16, cudaMemcpyHostToDevice, s));
+    Field xsv = op->xsv.view(k);
+    ColSet X = field_cols(xsv.v.data, f64, k, B->fsize(), k, true);
+    CUDA_CK(launch_gemm_ay(basis_cols(B, 0, l), B->Y.as<double>(), X, 0.0, op->ncomplex(), s));
+    CUDA_CK(launch_combine(x64, 1.0, x64, 1.0, xsv, s));
+    sync(s);  // Yr must outlive the async copy
+}
+
+}  // namespace eig
+
+// ======================================================================================
+// C ABI
+// ======================================================================================
+#define API_BEGIN try {
+#define API_END                                   \
+    }                                             \
+    catch (const eig::Error &e) {                 \
+        eig::set_error(e);                        \
+        return e.st;                              \
+    }                                             \
+    catch (const std::exception &e) {             \
+        eig::g_last_error = e.what();             \
+        return EIG_ERR_CUDA;                      \
+    }                                             \
+    return EIG_OK;
+
+#define ARG_CHECK(cond, msg)                                  \
+    do {                                                      \
+        if (!(cond)) throw eig::Error{EIG_ERR_ARG, (msg)};    \
+    } while (0)
+
+extern "C" {
+
+const char *eig_last_error(void) { return eig::g_last_error.c_str(); }
+
+eig_status eig_profile_enable(int on) {
+    API_BEGIN
+    eig::prof_enable(on != 0);
+    API_END
+}
+
+eig_status eig_profile_reset(void) {
+    API_BEGIN
+    eig::prof_reset();
+    API_END
+}
+
+eig_status eig_profile_read(eig_kernel_stat *out, int max, int *n) {
+    API_BEGIN
+    ARG_CHECK(n, "null argument");
+    static_assert(sizeof(eig_kernel_stat) == sizeof(eig::KernelStat), "layout");
+    *n = eig::prof_read(reinterpret_cast<eig::KernelStat *>(out), out ? max : 0);
+    API_END
+}
+
+eig_status eig_op_create(const double *gauge, const int dims[4], double m_q, const eig_op_opts *opts, eig_op *out) {
+    API_BEGIN
+    ARG_CHECK(gauge && dims && out, "null argument");
+    *out = nullptr;
+    long V = 1;
+    for (int i = 0; i < 4; i++) {
+        ARG_CHECK(dims[i] >= 2 && dims[i] <= 4096, "lattice extents must be in [2, 4096]");
+        V *= dims[i];
+    }
+    ARG_CHECK(V <= (1L << 27), "lattice too large");
+    ARG_CHECK(std::isfinite(m_q), "m_q must be finite");
+    eig_op_opts o;
+    if (opts) o = *opts;
+    else {
+        o.spinor_prec = EIG_PREC_F64;
+        o.link_compress12 = 1;
+        o.max_rhs = 1;
+        o.reliable_delta = 0.1;
+    }
+    ARG_CHECK(o.spinor_prec == 64 || o.spinor_prec == 32 || o.spinor_prec == 16, "spinor_prec must be 64, 32 or 16");
+    ARG_CHECK(o.max_rhs >= 1 && o.max_rhs <= MAX_RHS && (o.max_rhs & (o.max_rhs - 1)) == 0,
+              "max_rhs must be a power of two in [1, 16]");
+    std::unique_ptr<eig_op_s> op(new eig_op_s());
+    for (int i = 0; i < 4; i++) op->L[i] = dims[i];
+    op->V = V;
+    op->m_q = m_q;
+    op->prec = o.spinor_prec == 64 ? P64 : (o.spinor_prec == 32 ? P32 : P16);
+    op->wprec = op->prec == P64 ? P64 : P32;
+    op->gf_inner = op->prec == P64 ? GF_F64_18 : (op->prec == P32 ? (o.link_compress12 ? GF_F32_12 : GF_F32_18) : GF_F16_12);
+    op->max_rhs = o.max_rhs;
+    op->delta = (o.reliable_delta > 0.0 && o.reliable_delta < 1.0) ? o.reliable_delta : 0.1;
+    const int K = o.max_rhs;
+    // gauge: host -> device staging -> packed formats
+    eig::DevBuf stage;
+    stage.alloc((size_t)V * 4 * 9 * 16);
+    CUDA_CK(cudaMemcpy(stage.p, gauge, stage.n, cudaMemcpyHostToDevice));
+    op->gauge64.alloc((size_t)V * 4 * 9 * 16);
+    CUDA_CK(launch_pack_gauge(stage.as<double>(), op->gauge64.p, GF_F64_18, V, 0));
+    if (op->prec != P64) {
+        size_t gb = op->gf_inner == GF_F32_12 ? 48 : (op->gf_inner == GF_F32_18 ? 72 : 24);
+        op->gauge_in.alloc((size_t)V * 4 * gb);
+        CUDA_CK(launch_pack_gauge(stage.as<double>(), op->gauge_in.p, op->gf_inner, V, 0));
+    }
+    CUDA_CK(cudaDeviceSynchronize());
+    // workspace
+    op->r.alloc(op->prec, V, K);
+    op->p.alloc(op->prec, V, K);
+    op->u.alloc(op->prec, V, K);
+    op->b64.alloc(P64, V, K);
+    op->x64.alloc(P64, V, K);
+    op->u64.alloc(P64, V, K);
+    if (op->prec != P64) {
+        op->xlo.alloc(P32, V, K);
+        op->r64.alloc(P64, V, K);
+    }
+    op->rsv.alloc(op->wprec, V, K);
+    op->xsv.alloc(op->wprec, V, K);
+    op->nat_in.alloc((size_t)V * 12 * 16 * K);
+    op->nat_out.alloc((size_t)V * 12 * 16 * K);
+    op->st.alloc(sizeof(CGScalars) * MAX_RHS);
+    op->st_h.ensure(sizeof(CGScalars) * MAX_RHS);
+    op->red_partials.alloc((size_t)RED_BLOCKS * MAX_RHS * 64 * sizeof(double));
+    op->red_counter.alloc(64);
+    CUDA_CK(cudaMemset(op->red_counter.p, 0, 64));
+    op->ensure_history(1024, K);
+    *out = op.release();
+    API_END
+}
+
+eig_status eig_op_destroy(eig_op op) {
+    API_BEGIN
+    if (op) {
+        cudaDeviceSynchronize();
+        delete op;
+    }
+    API_END
+}
+
+eig_status eig_op_apply(eig_op op, int which, const double *in, double *out, int k, void *stream) {
+    API_BEGIN
+    ARG_CHECK(op && in && out, "null argument");
+    ARG_CHECK(which >= 0 && which <= 2, "which must be 0 (M), 1 (M^H) or 2 (A)");
+    ARG_CHECK(k >= 1 && k <= op->max_rhs && (k & (k - 1)) == 0, "k must be a power of two <= max_rhs");
+    std::lock_guard<std::mutex> lk(op->mu);
+    cudaStream_t s = (cudaStream_t)stream;
+    Field x64 = op->x64.view(k);
+    load_natural(op, in, x64, s);
+    Field a = op->p.view(k), b = op->u.view(k), c = op->r.view(k);
+    CUDA_CK(launch_combine(a, 1.0, x64, 0.0, null_field(), s));
+    const bool f64 = op->prec == P64;
+    if (which == 0) apply_M(op, a, b, false, f64, s);
+    else if (which == 1) apply_M(op, a, b, true, f64, s);
+    else {
+        apply_M(op, a, c, false, f64, s);
+        apply_M(op, c, b, true, f64, s);
+    }
+    CUDA_CK(launch_combine(x64, 1.0, b, 0.0, null_field(), s));
+    store_natural(op, x64, out, s);
+    sync(s);
+    API_END
+}
+
+eig_status eig_basis_create(eig_op op, int max_vecs, eig_basis *out) {
+    API_BEGIN
+    ARG_CHECK(op && out, "null argument");
+    ARG_CHECK(max_vecs >= 1 && max_vecs <= 256, "max_vecs must be in [1, 256]");
+    *out = nullptr;
+    std::unique_ptr<eig_basis_s> B(new eig_basis_s());
+    B->op = op;
+    B->max_vecs = max_vecs;
+    B->U.alloc((size_t)max_vecs * op->wfield_bytes());
+    B->pend.alloc((size_t)MAX_NEV * op->wfield_bytes());
+    B->W.alloc((size_t)MAX_NEV * op->wfield_bytes());
+    *out = B.release();
+    API_END
+}
+
+eig_status eig_basis_destroy(eig_basis basis) {
+    API_BEGIN
+    if (basis) {
+        cudaDeviceSynchronize();
+        delete basis;
+    }
+    API_END
+}
+
+eig_status eig_basis_size(eig_basis basis, int *l) {
+    API_BEGIN
+    ARG_CHECK(basis && l, "null argument");
+    *l = basis->l;
+    API_END
+}
+
+eig_status eig_basis_truncate(eig_basis basis, int l) {
+    API_BEGIN
+    ARG_CHECK(basis, "null argument");
+    ARG_CHECK(l >= 0 && l <= basis->l, "l must be in [0, current size]");
+    std::lock_guard<std::mutex> lk(basis->mu);
+    const int old = basis->l;
+    std::vector<cd> H((size_t)l * l);
+    for (int a = 0; a < l; a++)
+        for (int b = 0; b < l; b++) H[(size_t)a * l + b] = basis->H[(size_t)a * old + b];
+    basis->H = H;
+    basis->l = l;
+    basis->npend = 0;
+    refactor(basis);
+    API_END
+}
+
+eig_status eig_eigcg_solve(eig_op op, eig_basis basis, const double *b, double *x, int nev, int m, double tol,
+                           int max_iter, eig_stats *stats, void *stream) {
+    API_BEGIN
+    ARG_CHECK(op && b && x, "null argument");
+    ARG_CHECK(nev >= 1 && nev <= MAX_NEV, "nev must be in [1, 16]");
+    ARG_CHECK(m > 2 * nev && m <= MAX_WINDOW, "need 2*nev < m <= 128");
+    ARG_CHECK(tol > 0.0 && tol < 1.0, "tol must be in (0, 1)");
+    ARG_CHECK(max_iter >= 1 && max_iter <= 10000000, "max_iter out of range");
+    ARG_CHECK(!basis || basis->op == op, "basis belongs to another op");
+    std::lock_guard<std::mutex> lk(op->mu);
+    auto t0 = std::chrono::steady_clock::now();
+    cudaStream_t s = (cudaStream_t)stream;
+    // window storage: m + 1 slots, t_prev, t_cur
+    const size_t fb = op->wfield_bytes();
+    if (op->win_slots < m + 1) {
+        op->win.alloc((size_t)(m + 1) * fb);
+        op->win_slots = m + 1;
+    }
+    op->tprev.ensure(fb);
+    op->tcur.ensure(fb);
+    op->col_off.ensure(MAX_WINDOW * sizeof(long));
+    op->qz.ensure((size_t)MAX_WINDOW * 2 * MAX_NEV * 16);
+    op->wv.ensure(2 * MAX_NEV * 16);
+    Solve sv = make_solve(op, 1, s, max_iter);
+    load_natural(op, b, sv.b64, s);
+    load_natural(op, x, sv.x64, s);
+    if (basis && basis->l > 0) {
+        // init-CG part of the Sec. 4 box: x0 = x~0 + U H^{-1} U^H (b - A x~0)
+        apply_A64(op, sv.x64, sv.r64, s);
+        CUDA_CK(launch_combine(sv.r64, 1.0, sv.b64, -1.0, sv.r64, s));
+        deflate_into(basis, sv.r64, sv.x64, s);
+    }
+    sv.start(tol);
+    Window w;
+    w.nev = nev;
+    w.m = m;
+    for (int q = m; q >= 0; q--) w.freel.push_back(q);  // slot 0 popped first
+    int rounds = 0;
+    bool ok = true;
+    while (true) {
+        ok = cg_run(sv, max_iter, &w, op);
+        if (!ok) break;
+        if (!cg_finish(sv, max_iter, &w, op, rounds)) break;
+    }
+    // eigCG output: nev lowest Ritz pairs of the final window
+    int nr = 0;
+    const int J = sv.j;
+    if (w.i > 0) {
+        sv.read_history(J);
+        std::vector<cd> T;
+        window_T(w, w.i, sv.ha(), sv.hb(), sv.hr(), T);
+        nr = std::min(nev, w.i);
+        std::vector<double> ev(nr);
+        std::vector<cd> Y((size_t)w.i * nr);
+        dense::window_lowest(w.i, T.data(), w.kh, w.i, nr, ev.data(), Y.data());
+        if (basis) {
+            std::vector<long> off(w.i);
+            const long fs = op->ncomplex();
+            for (int a = 0; a < w.i; a++) off[a] = (long)w.slots[a] * fs;
+            CUDA_CK(cudaMemcpyAsync(op->col_off.p, off.data(), w.i * sizeof(long), cudaMemcpyHostToDevice, s));
+            std::vector<double> yr((size_t)w.i * nr * 2);
+            for (int a = 0; a < w.i; a++)
+                for (int c = 0; c < nr; c++) {
+                    yr[((size_t)a * nr + c) * 2] = Y[(size_t)c * w.i + a].real();
+                    yr[((size_t)a * nr + c) * 2 + 1] = Y[(size_t)c * w.i + a].imag();
+                }
+            basis->Y.ensure(yr.size() * sizeof(double));
+            CUDA_CK(cudaMemcpyAsync(basis->Y.p, yr.data(), yr.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+            ColSet A;
+            A.base = op->win.p;
+            A.f64 = op->wprec == P64;
+            A.ki = 1;
+            A.col_stride = 0;
+            A.ncols = w.i;
+            A.col_off = op->col_off.as<long>();
+            ColSet O = field_cols(basis->pend.p, A.f64, 1, basis->fsize(), nr, false);
+            CUDA_CK(launch_gemm_ay(A, basis->Y.as<double>(), O, 0.0, op->ncomplex(), s));
+            sync(s);
+            basis->npend = nr;
+            basis->pend_ritz = ev;
+        }
+    } else if (basis) {
+        basis->npend = 0;
+    }
+    store_natural(op, sv.x64, x, s);
+    sync(s);
+    if (stats) {
+        stats->iters = J;
+        stats->restarts = w.restarts;
+        int rel = 0;
+        for (int v : sv.reliable) rel += v;
+        stats->reliable_updates = rel;
+        const double bn2 = sv.sth[0].target / (tol * tol);
+        stats->true_rel_res = bn2 > 0 ? std::sqrt(sv.sth[0].aux / bn2) : 0.0;
+        stats->converged = stats->true_rel_res <= tol * (1 + 1e-12) ? 1 : 0;
+        stats->n_ritz = nr;
+        stats->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
+    if (!ok) {
+        eig::g_last_error = "max_iter reached";
+        return EIG_NOT_CONVERGED;
+    }
+    API_END
+}
+
+eig_status eig_basis_grow(eig_basis B, void *stream) {
+    API_BEGIN
+    ARG_CHECK(B, "null argument");
+    std::lock_guard<std::mutex> lk(B->mu);
+    std::lock_guard<std::mutex> lk2(B->op->mu);
+    eig_op_s *op = B->op;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int np = B->npend;
+    if (np == 0) return EIG_OK;
+    const int l = B->l;
+    const bool f64 = op->wprec == P64;
+    const long nrow = op->ncomplex();
+    ColSet P = field_cols(B->pend.p, f64, 1, B->fsize(), np, false);
+    // classical Gram-Schmidt against U, twice
+    if (l > 0) {
+        B->C.ensure((size_t)l * np * 16);
+        B->Ch.ensure((size_t)l * np * 16);
+        for (int pass = 0; pass < 2; pass++) {
+            CUDA_CK(launch_gemm_ahb(basis_cols(B, 0, l), P, nrow, B->C.as<double>(), op->red(), s));
+            CUDA_CK(cudaMemcpyAsync(B->Ch.p, B->C.p, (size_t)l * np * 16, cudaMemcpyDeviceToHost, s));
+            sync(s);
+            std::vector<double> negc((size_t)l * np * 2);
+            const double *c = B->Ch.as<double>();
+            for (size_t q = 0; q < negc.size(); q++) negc[q] = -c[q];
+            B->Y.ensure(negc.size() * sizeof(double));
+            CUDA_CK(cudaMemcpyAsync(B->Y.p, negc.data(), negc.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+            CUDA_CK(launch_gemm_ay(basis_cols(B, 0, l), B->Y.as<double>(), P, 1.0, nrow, s));
+            sync(s);
+        }
+    }
+    // orthonormalise the remainders among themselves: pivoted Cholesky of the Gram matrix
+    B->C.ensure((size_t)np * np * 16);
+    B->Ch.ensure((size_t)np * np * 16);
+    CUDA_CK(launch_gemm_ahb(P, P, nrow, B->C.as<double>(), op->red(), s));
+    CUDA_CK(cudaMemcpyAsync(B->Ch.p, B->C.p, (size_t)np * np * 16, cudaMemcpyDeviceToHost, s));
+    sync(s);
+    std::vector<cd> G(B->Ch.as<cd>(), B->Ch.as<cd>() + (size_t)np * np);
+    // Gram-Schmidt in coefficient space: columns of R^{-1} for the kept vectors
+    const double drop = f64 ? 1e-10 : 1e-4;
+    std::vector<cd> Rinv((size_t)np * np, cd(0.0));  // column c: coefficients of kept vector c
+    std::vector<int> keep;
+    for (int c = 0; c < np; c++) {
+        // coefficient vector e_c projected against kept ones (in the G inner product), twice
+        std::vector<cd> v(np, cd(0.0));
+        v[c] = 1.0;
+        for (int pass = 0; pass < 2; pass++)
+            for (int q = 0; q < (int)keep.size(); q++) {
+                const cd *u = &Rinv[(size_t)q * np];
+                cd dot = 0.0;  // u^H G v
+                for (int a = 0; a < np; a++)
+                    for (int bb = 0; bb < np; bb++) dot += std::conj(u[a]) * G[(size_t)a * np + bb] * v[bb];
+                for (int a = 0; a < np; a++) v[a] -= dot * u[a];
+            }
+        cd nn = 0.0;
+        for (int a = 0; a < np; a++)
+            for (int bb = 0; bb < np; bb++) nn += std::conj(v[a]) * G[(size_t)a * np + bb] * v[bb];
+        const double nv = std::sqrt(std::max(0.0, nn.real()));
+        if (nv <= drop) continue;
+        const int q = (int)keep.size();
+        for (int a = 0; a < np; a++) Rinv[(size_t)q * np + a] = v[a] / nv;
+        keep.push_back(c);
+    }
+    const int r = (int)keep.size();
+    if (r == 0) {
+        B->npend = 0;
+        return EIG_OK;
+    }
+    if (l + r > B->max_vecs) throw Error{EIG_ERR_BUDGET, "basis full (max_vecs reached)"};
+    // U[:, l + c] = P Rinv[:, c]
+    std::vector<double> yr((size_t)np * r * 2);
+    for (int a = 0; a < np; a++)
+        for (int c = 0; c < r; c++) {
+            yr[((size_t)a * r + c) * 2] = Rinv[(size_t)c * np + a].real();
+            yr[((size_t)a * r + c) * 2 + 1] = Rinv[(size_t)c * np + a].imag();
+        }
+    B->Y.ensure(yr.size() * sizeof(double));
+    CUDA_CK(cudaMemcpyAsync(B->Y.p, yr.data(), yr.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    CUDA_CK(launch_gemm_ay(P, B->Y.as<double>(), basis_cols(B, l, r), 0.0, nrow, s));
+    // W = A V-bar with the FP64 operator, stored in window precision
+    Field x64 = op->x64.view(1), r64f = op->b64.view(1);
+    for (int c = 0; c < r; c++) {
+        Field uc = field_at(op->wprec, (char *)B->U.p + (size_t)(l + c) * op->wfield_bytes(), op->V, 1);
+        Field wc = field_at(op->wprec, (char *)B->W.p + (size_t)c * op->wfield_bytes(), op->V, 1);
+        CUDA_CK(launch_combine(x64, 1.0, uc, 0.0, null_field(), s));
+        apply_A64(op, x64, r64f, s);
+        CUDA_CK(launch_combine(wc, 1.0, r64f, 0.0, null_field(), s));
+    }
+    ColSet Wc = field_cols(B->W.p, f64, 1, B->fsize(), r, false);
+    const int ln = l + r;
+    B->C.ensure((size_t)ln * r * 16);
+    B->Ch.ensure((size_t)ln * r * 16);
+    CUDA_CK(launch_gemm_ahb(basis_cols(B, 0, ln), Wc, nrow, B->C.as<double>(), op->red(), s));
+    CUDA_CK(cudaMemcpyAsync(B->Ch.p, B->C.p, (size_t)ln * r * 16, cudaMemcpyDeviceToHost, s));
+    sync(s);
+    const cd *UW = B->Ch.as<cd>();  // (l + r) x r: rows 0..l-1 = U^H W, rows l.. = V-bar^H W
+    std::vector<cd> Hn((size_t)ln * ln);
+    for (int a = 0; a < l; a++)
+        for (int bb = 0; bb < l; bb++) Hn[(size_t)a * ln + bb] = B->H[(size_t)a * l + bb];
+    for (int a = 0; a < l; a++)
+        for (int c = 0; c < r; c++) {
+            Hn[(size_t)a * ln + l + c] = UW[(size_t)a * r + c];
+            Hn[(size_t)(l + c) * ln + a] = std::conj(UW[(size_t)a * r + c]);
+        }
+    for (int a = 0; a < r; a++)
+        for (int c = 0; c < r; c++) {
+            const cd v = 0.5 * (UW[(size_t)(l + a) * r + c] + std::conj(UW[(size_t)(l + c) * r + a]));
+            Hn[(size_t)(l + a) * ln + l + c] = v;
+        }
+    B->H = Hn;
+    B->l = ln;
+    B->npend = 0;
+    refactor(B);
+    if (!B->chol_ok) throw Error{EIG_ERR_BREAKDOWN, "H = U^H A U lost positive definiteness"};
+    API_END
+}
+
+eig_status eig_basis_deflate(eig_basis B, const double *b, const double *x_in, double *x0, int k, void *stream) {
+    API_BEGIN
+    ARG_CHECK(B && b && x0, "null argument");
+    eig_op_s *op = B->op;
+    ARG_CHECK(k >= 1 && k <= op->max_rhs && (k & (k - 1)) == 0, "k must be a power of two <= max_rhs");
+    std::lock_guard<std::mutex> lk(B->mu);
+    std::lock_guard<std::mutex> lk2(op->mu);
+    cudaStream_t s = (cudaStream_t)stream;
+    Field b64 = op->b64.view(k), x64 = op->x64.view(k), r64 = (op->prec == P64 ? op->r : op->r64).view(k);
+    load_natural(op, b, b64, s);
+    if (x_in) {
+        load_natural(op, x_in, x64, s);
+        apply_A64(op, x64, r64, s);
+        CUDA_CK(launch_combine(r64, 1.0, b64, -1.0, r64, s));
+    } else {
+        zero_field(x64, s);
+        CUDA_CK(launch_combine(r64, 1.0, b64, 0.0, null_field(), s));
+    }
+    deflate_into(B, r64, x64, s);
+    store_natural(op, x64, x0, s);
+    sync(s);
+    API_END
+}
+
+eig_status eig_initcg_solve(eig_op op, eig_basis basis, const double *b, double *x, double tol, double restart_tol,
+                            int max_iter, int k, eig_stats *stats, void *stream) {
+    API_BEGIN
+    ARG_CHECK(op && b && x, "null argument");
+    ARG_CHECK(k >= 1 && k <= op->max_rhs && (k & (k - 1)) == 0, "k must be a power of two <= max_rhs");
+    ARG_CHECK(tol > 0.0 && tol < 1.0, "tol must be in (0, 1)");
+    ARG_CHECK(max_iter >= 1 && max_iter <= 10000000, "max_iter out of range");
+    ARG_CHECK(!basis || basis->op == op, "basis belongs to another op");
+    std::lock_guard<std::mutex> lk(op->mu);
+    auto t0 = std::chrono::steady_clock::now();
+    cudaStream_t s = (cudaStream_t)stream;
+    Solve sv = make_solve(op, k, s, max_iter);
+    load_natural(op, b, sv.b64, s);
+    load_natural(op, x, sv.x64, s);
+    const bool defl = basis && basis->l > 0;
+    if (defl) {
+        apply_A64(op, sv.x64, sv.r64, s);
+        CUDA_CK(launch_combine(sv.r64, 1.0, sv.b64, -1.0, sv.r64, s));
+        deflate_into(basis, sv.r64, sv.x64, s);
+    }
+    int restarts = 0;
+    bool ok = true;
+    int rounds = 0;
+    if (defl && restart_tol > tol) {
+        // phase 1: CG to restart_tol, then re-deflate from the current x (Sec. 5.3)
+        sv.start(restart_tol);
+        ok = cg_run(sv, max_iter, nullptr, op);
+        const int j1 = sv.j;
+        std::vector<int> rel1 = sv.reliable;
+        if (ok) {
+            sv.true_residual(false);  // x64 += x_lo; r64 = b - A x64
+            deflate_into(basis, sv.r64, sv.x64, s);
+            restarts = 1;
+            sv.start(tol);
+            sv.j = j1;
+            sv.j_checked = j1;
+            for (int q = 0; q < k; q++) sv.reliable[q] += rel1[q];
+            for (int q = 0; q < k; q++) sv.sth[q].iters = j1;
+            sv.write_scalars();
+        }
+    } else {
+        sv.start(tol);
+    }
+    while (ok) {
+        ok = cg_run(sv, max_iter, nullptr, op);
+        if (!ok) break;
+        if (!cg_finish(sv, max_iter, nullptr, op, rounds)) break;
+    }
+    if (!ok) sv.true_residual(false), sv.read_scalars();
+    store_natural(op, sv.x64, x, s);
+    sync(s);
+    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (stats) {
+        for (int q = 0; q < k; q++) {
+            eig_stats &st = stats[q];
+            st.iters = sv.sth[q].iters;
+            st.restarts = restarts;
+            st.reliable_updates = sv.reliable[q];
+            const double bn2 = sv.sth[q].target / (tol * tol);
+            st.true_rel_res = bn2 > 0 ? std::sqrt(sv.sth[q].aux / bn2) : 0.0;
+            st.converged = st.true_rel_res <= tol * (1 + 1e-12) ? 1 : 0;
+            st.n_ritz = 0;
+            st.ms = ms;
+        }
+    }
+    if (!ok) {
+        eig::g_last_error = "max_iter reached";
+        return EIG_NOT_CONVERGED;
+    }
+    API_END
+}
+
+eig_status eig_basis_ritz(eig_basis B, double *evals, double *resnorms, int *n, void *stream) {
+    API_BEGIN
+    ARG_CHECK(B && evals && n, "null argument");
+    std::lock_guard<std::mutex> lk(B->mu);
+    std::lock_guard<std::mutex> lk2(B->op->mu);
+    eig_op_s *op = B->op;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int l = B->l;
+    *n = l;
+    if (l == 0) return EIG_OK;
+    std::vector<double> th(l);
+    std::vector<cd> S((size_t)l * l);
+    dense::herm_eig_lowest(l, B->H.data(), l, th.data(), S.data());
+    for (int a = 0; a < l; a++) evals[a] = th[a];
+    if (!resnorms) return EIG_OK;
+    const bool f64 = op->wprec == P64;
+    Field x64 = op->x64.view(1), r64f = op->b64.view(1);
+    Field w64 = op->prec == P64 ? op->r.view(1) : op->r64.view(1);
+    for (int c0 = 0; c0 < l; c0 += MAX_NEV) {
+        const int nc = std::min(MAX_NEV, l - c0);
+        std::vector<double> yr((size_t)l * nc * 2);
+        for (int a = 0; a < l; a++)
+            for (int c = 0; c < nc; c++) {
+                yr[((size_t)a * nc + c) * 2] = S[(size_t)(c0 + c) * l + a].real();
+                yr[((size_t)a * nc + c) * 2 + 1] = S[(size_t)(c0 + c) * l + a].imag();
+            }
+        B->Y.ensure(yr.size() * sizeof(double));
+        CUDA_CK(cudaMemcpyAsync(B->Y.p, yr.data(), yr.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+        ColSet Wc = field_cols(B->W.p, f64, 1, B->fsize(), nc, false);
+        CUDA_CK(launch_gemm_ay(basis_cols(B, 0, l), B->Y.as<double>(), Wc, 0.0, op->ncomplex(), s));
+        for (int c = 0; c < nc; c++) {
+            Field wc = field_at(op->wprec, (char *)B->W.p + (size_t)c * op->wfield_bytes(), op->V, 1);
+            CUDA_CK(launch_combine(x64, 1.0, wc, 0.0, null_field(), s));
+            apply_A64(op, x64, r64f, s);
+            CUDA_CK(launch_combine(w64, 1.0, r64f, -th[c0 + c], x64, s));
+            CUDA_CK(launch_norm2(w64, op->st.as<CGScalars>(), false, op->history(1), 0, op->red(), s));
+            CGScalars h;
+            CUDA_CK(cudaMemcpyAsync(&h, op->st.p, sizeof(h), cudaMemcpyDeviceToHost, s));
+            sync(s);
+            resnorms[c0 + c] = std::sqrt(h.aux);
+        }
+    }
+    API_END
+}
+
+eig_status eig_basis_vector(eig_basis B, int j, double *out, void *stream) {
+    API_BEGIN
+    ARG_CHECK(B && out, "null argument");
+    ARG_CHECK(j >= 0 && j < B->l, "j out of range");
+    std::lock_guard<std::mutex> lk(B->op->mu);
+    eig_op_s *op = B->op;
+    cudaStream_t s = (cudaStream_t)stream;
+    Field uc = field_at(op->wprec, (char *)B->U.p + (size_t)j * op->wfield_bytes(), op->V, 1);
+    Field x64 = op->x64.view(1);
+    CUDA_CK(launch_combine(x64, 1.0, uc, 0.0, null_field(), s));
+    store_natural(op, x64, out, s);
+    sync(s);
+    API_END
+}
+
+eig_status eig_basis_h(eig_basis B, double *out) {
+    API_BEGIN
+    ARG_CHECK(B && out, "null argument");
+    memcpy(out, B->H.data(), B->H.size() * sizeof(cd));
+    API_END
+}
+
+}  // extern "C"

@@ -1,0 +1,126 @@
+// Host-side launchers of the CUDA kernels (definitions in dslash.cu, blas.cu, gemm.cu).
+// Every launcher enqueues on `stream` and returns the launch status.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace eig {
+
+enum Prec { P64 = 0, P32 = 1, P16 = 2 };
+
+inline size_t field_bytes(Prec p, long V, int k) {
+    switch (p) {
+        case P64: return (size_t)V * k * 192;
+        case P32: return (size_t)V * k * 96;
+        default: return (size_t)V * k * 48;
+    }
+}
+
+// Per-RHS CG scalars, FP64, resident on the device.
+struct CGScalars {
+    double rho;       // r^H r of the current residual
+    double rho_prev;  // previous rho
+    double alpha;     // alpha_j of the current iteration
+    double beta;      // beta of the next p update
+    double pAp;       // p^H A p = ||M p||^2
+    double target;    // stop when rho <= target (tol^2 ||b||^2)
+    double aux;       // last auxiliary reduction (true residual norm^2, norm of b, ...)
+    int active;       // 1 while iterating
+    int iters;        // last iteration in which this RHS was active
+    int breakdown;    // 1 if pAp <= 0, NaN or Inf was met
+};
+
+// Reduction scratch shared by the kernels of one solver stream.
+struct RedScratch {
+    double *partials;   // [max_blocks * MAX_RHS * 64] doubles
+    unsigned *counter;  // one counter, zero between launches
+    int max_blocks;
+};
+
+struct Field {
+    Prec prec;
+    FieldView v;
+};
+
+// History of CG scalars: alpha[j*k + r] etc. for iterations j = 0..cap-1.
+struct History {
+    double *alpha;
+    double *beta;
+    double *rho;
+    int cap;
+};
+
+struct DslashCall {
+    Field in, out;     // out may be unused by the CG epilogue (store_out = 0)
+    GaugeView gauge;
+    int gformat;       // GaugeFormat
+    int L[4];
+    long V;
+    int k;
+    double diag;       // 4 + m_q
+    bool dagger;
+};
+
+// ---------------------------- dslash.cu ----------------------------------------------
+// out = M in (dagger: M^H in)
+cudaError_t launch_dslash(const DslashCall &c, cudaStream_t s);
+// CG pass 1: out = M in, pAp = ||out||^2, alpha = rho / pAp   (Fig. 1 steps 11-12)
+cudaError_t launch_dslash_norm(const DslashCall &c, CGScalars *st, History h, int iter, RedScratch red,
+                               cudaStream_t s);
+// CG pass 2: t = M^H in; x += alpha p; r -= alpha t; rho_new = ||r||^2; beta = rho_new / rho
+// (Fig. 1 steps 11-14 and 4/8 of the next iteration).  If t_save.v.data != nullptr, t is
+// also written there (window precision).
+cudaError_t launch_dslash_cg(const DslashCall &c, Field p, Field x, Field r, Field t_save, CGScalars *st, History h,
+                             int iter, RedScratch red, cudaStream_t s);
+// FP64 residual: r = b - M^H in, aux = ||r||^2 (with set_rho: rho = aux, beta = rho / rho_prev,
+// history beta[iter + 1] = beta, rho[iter] = rho).
+cudaError_t launch_dslash_resid(const DslashCall &c, Field b, Field r, CGScalars *st, History h, int iter,
+                                bool set_rho, RedScratch red, cudaStream_t s);
+
+// ---------------------------- blas.cu -------------------------------------------------
+// natural FP64 [k][V][12] complex  <->  internal field
+cudaError_t launch_pack(const double *nat, Field f, cudaStream_t s);
+cudaError_t launch_unpack(Field f, double *nat, cudaStream_t s);
+// gauge natural [V][4][3][3] complex (device) -> internal format
+cudaError_t launch_pack_gauge(const double *nat, void *dst, int gformat, long V, cudaStream_t s);
+// out = ca * a + cb * b   (b may have data == nullptr; ca, cb real).  All fields same V, k.
+cudaError_t launch_combine(Field out, double ca, Field a, double cb, Field b, cudaStream_t s);
+// per-RHS ||f||^2 -> st[r].aux;  with as_rho: also rho = aux, rho_prev = aux, history rho[iter]
+// and target = tol2 * bnorm2[r] computed elsewhere (untouched here).
+cudaError_t launch_norm2(Field f, CGScalars *st, bool as_rho, History h, int iter, RedScratch red, cudaStream_t s);
+// CG step 9 + eigCG step 11.13: p = r + beta p (first: p = r); optionally v = r / sqrt(rho)
+cudaError_t launch_pupdate(Field r, Field p, bool first, CGScalars *st, Field v_append, cudaStream_t s);
+// set up per-RHS scalars: target = tol^2 * aux (aux must hold ||b||^2), active = 1, breakdown = 0
+cudaError_t launch_cg_init(CGScalars *st, int k, double tol, History h, cudaStream_t s);
+
+// ---------------------------- gemm.cu -------------------------------------------------
+// A column set of complex vectors stored in fields of one precision (double or float).
+// Element (row, col) sits at complex index
+//   ((row / cpc) * ki + (col % ki)) * cpc + row % cpc + (col / ki) * col_stride
+// where cpc = complex numbers per storage chunk (1 for FP64, 2 for FP32): ki = k for
+// an RHS-inner field of k RHS, ki = 1 and col_stride = field size for separate fields.
+// `cols` gives per-column base offsets (in complex units) when non-null (window slots).
+struct ColSet {
+    void *base;
+    bool f64;
+    int ki;
+    long col_stride;
+    int ncols;
+    const long *col_off;  // device array of ncols offsets, or nullptr
+};
+
+// C (nA x nB, FP64 complex, row-major, device) = A^H B over nrows complex rows.
+cudaError_t launch_gemm_ahb(ColSet A, ColSet B, long nrows, double *C, RedScratch red, cudaStream_t s);
+// Out[:, c] = beta_out * Out[:, c] + sum_a A[:, a] Y[a, c]   (Y: nA x nOut FP64 complex row-major, device)
+cudaError_t launch_gemm_ay(ColSet A, const double *Y, ColSet Out, double beta_out, long nrows, cudaStream_t s);
+// eigCG restart (Fig. 1 step 11.7 + 11.8): in place over the window slots,
+//   V[:, c] = sum_a V[:, a] QZ[a, c]  (c < nout), and  wv[c] = sum_rows conj(w) V_new[:, c],
+//   w = t - beta * t_prev  (beta read from *beta_dev).  wv: FP64 complex [nout], device.
+cudaError_t launch_window_restart(ColSet Vw, int m, const double *QZ, int nout, const void *t, const void *t_prev,
+                                  const double *beta_dev, long nrows, double *wv, RedScratch red, cudaStream_t s);
+
+int device_sm_count();
+
+}  // namespace eig

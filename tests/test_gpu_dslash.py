@@ -1,0 +1,96 @@
+"""GPU parity of the Wilson matvec (Fig. 1 step 11) through the C ABI against the oracle.
+
+Relative error ||y_gpu - y_oracle|| / ||y_oracle|| per RHS: FP64 <= 1e-12, FP32
+<= 1e-6, FP16 storage <= 5e-3, for M, M^H and A = M^H M, single and multi-RHS.
+Lattices: 4^4, an anisotropic 6x4x2x10 (extents 2 and a site count that is not a
+multiple of the block size), 8^4, and the 24^3x64 workload of the benchmark at
+k = 16 in FP32 with 12-real links.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_0707_0131_gb300 import fixtures as fx
+
+pytestmark = pytest.mark.gpu
+
+TOL = {64: 1e-12, 32: 1e-6, 16: 5e-3}
+
+
+@pytest.fixture(scope="module")
+def api():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_0707_0131_gb300 import api as a
+
+    return a
+
+
+def _relerr(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (6, 4, 2, 10), (8, 8, 8, 8)])
+@pytest.mark.parametrize("prec", [64, 32, 16])
+@pytest.mark.parametrize("k", [1, 4])
+def test_matvec_parity(api, dims, prec, k):
+    m_q = 0.05
+    gauge = fx.make_gauge(dims, 31)
+    W = oracle.Wilson(dims, m_q, gauge)
+    op = api.Op(gauge, dims, m_q, prec=prec, max_rhs=k)
+    psi = fx.make_rhs(dims, 32, k)
+    for which, f in [(0, W.M), (1, W.Mdag), (2, W.A)]:
+        out = np.empty_like(psi)
+        op.apply(which, psi, out, k)
+        for r in range(k):
+            err = _relerr(out[r].reshape(-1), f(psi[r]))
+            assert err < TOL[prec], (which, r, err)
+    op.close()
+
+
+def test_matvec_fp32_uncompressed_links(api):
+    dims = (6, 4, 2, 10)
+    gauge = fx.make_gauge(dims, 33)
+    W = oracle.Wilson(dims, -0.1, gauge)
+    op = api.Op(gauge, dims, -0.1, prec=32, compress12=False)
+    psi = fx.make_rhs(dims, 34, 1)
+    out = op.A(psi)
+    assert _relerr(out[0].reshape(-1), W.A(psi[0])) < 1e-6
+
+
+def test_free_field_eigenvector(api):
+    """Plane wave at p = 0 is an eigenvector of A with eigenvalue m^2 (free field)."""
+    dims = (4, 4, 4, 8)
+    m = 0.2
+    op = api.Op(fx.unit_gauge(dims), dims, m, prec=64)
+    psi = np.zeros((1, fx.volume(dims), 4, 3), dtype=np.complex128)
+    psi[0, :, 1, 2] = 1.0
+    out = op.A(psi)
+    assert np.max(np.abs(out - m * m * psi)) < 1e-14
+
+
+@pytest.mark.slow
+def test_matvec_bench_workload_fp32_k16(api):
+    """24^3x64, FP32 storage, 12-real links, 16 RHS per launch (the benchmark's launch)."""
+    import torch
+
+    masses = json.load(open(os.path.join(os.path.dirname(__file__), "..", "configs", "masses.json")))
+    name = "24^3x64"
+    dims = fx.LATTICES[name]
+    m_q = masses.get(name, {}).get("1e+05", {}).get("m_q", -0.2)
+    gauge = fx.make_gauge(dims, fx.GAUGE_SEEDS[name])
+    W = oracle.Wilson(dims, m_q, gauge)
+    op = api.Op(gauge, dims, m_q, prec=32, max_rhs=16)
+    psi = fx.make_rhs(dims, 35, 16)
+    d_in = torch.from_numpy(psi).cuda()
+    d_out = torch.empty_like(d_in)
+    op.apply(2, d_in, d_out, 16)
+    out = d_out.cpu().numpy()
+    for r in (0, 7, 15):
+        assert _relerr(out[r].reshape(-1), W.A(psi[r])) < 1e-6
+    op.close()

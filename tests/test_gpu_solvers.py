@@ -1,0 +1,235 @@
+"""GPU parity of the solvers (CG, eigCG, Incremental eigCG, init-CG) against the oracle.
+
+Bars (stated with the method): FP64 true residual ||b - A x|| / ||b|| <= tol
+recomputed by the oracle; iteration counts within 10% of the oracle's; converged
+Ritz values within 1e-6 relative; the Galerkin condition of Eq. 1 holds for the
+GPU's own basis.  Mixed precision reaches tol through reliable updates.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import solvers
+from paper_0707_0131_gb300 import fixtures as fx
+
+pytestmark = pytest.mark.gpu
+
+MASSES = json.load(open(os.path.join(os.path.dirname(__file__), "..", "configs", "masses.json")))
+
+
+@pytest.fixture(scope="module")
+def api():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_0707_0131_gb300 import api as a
+
+    return a
+
+
+@pytest.fixture(scope="module")
+def small():
+    dims = fx.LATTICES["4^4"]
+    m_q = MASSES["4^4"]["1e+03"]["m_q"]
+    gauge = fx.make_gauge(dims, fx.GAUGE_SEEDS["4^4"])
+    W = oracle.Wilson(dims, m_q, gauge)
+    bs = [fx.make_rhs(dims, fx.rhs_seed("4^4", r))[0].reshape(-1) for r in range(8)]
+    return dims, m_q, gauge, W, bs
+
+
+def _true_res(W, x, b):
+    return np.linalg.norm(b - W.A(x)) / np.linalg.norm(b)
+
+
+def _close_iters(a, b, frac=0.1):
+    return abs(a - b) <= max(1, frac * b)
+
+
+def test_cg_parity_fp64(api, small):
+    dims, m_q, gauge, W, bs = small
+    op = api.Op(gauge, dims, m_q, prec=64)
+    x = np.zeros_like(bs[0])
+    st = op.initcg_solve(bs[0], x, tol=1e-10)[0]
+    o = solvers.cg(W, bs[0], tol=1e-10)
+    assert _close_iters(st["iters"], o["iters"]), (st, o["iters"])
+    assert _true_res(W, x, bs[0]) <= 1e-10
+    assert np.linalg.norm(x - o["x"]) / np.linalg.norm(o["x"]) < 1e-7
+    op.close()
+
+
+def test_eigcg_parity_fp64(api, small):
+    """Config 'plain small': eigCG(8, 24), tol 1e-10, 4^4, cond ~ 1e3."""
+    dims, m_q, gauge, W, bs = small
+    op = api.Op(gauge, dims, m_q, prec=64)
+    basis = api.Basis(op, 32)
+    x = np.zeros_like(bs[0])
+    st = op.eigcg_solve(bs[0], x, nev=8, m=24, tol=1e-10, basis=basis)
+    o = solvers.eigcg(W, bs[0], nev=8, m=24, tol=1e-10)
+    assert st["restarts"] >= 3 and st["n_ritz"] == 8
+    assert _close_iters(st["iters"], o["iters"]), (st["iters"], o["iters"])
+    assert _true_res(W, x, bs[0]) <= 1e-10
+    basis.grow()
+    theta, res = basis.ritz()
+    # converged Ritz pairs (oracle residual below 1e-8 ||A||) agree to 1e-6 relative
+    lam_max = 64.0
+    Vo = o["V"]
+    ores = np.array([np.linalg.norm(W.A(Vo[:, c]) - o["ritz"][c] * Vo[:, c]) for c in range(Vo.shape[1])])
+    conv = ores < 1e-8 * lam_max
+    assert conv.sum() >= 2
+    rel = np.abs(np.sort(theta)[: len(conv)][conv] - o["ritz"][conv]) / o["ritz"][conv]
+    assert np.all(rel < 1e-6), rel
+    # all Ritz values lie above the exact eigenvalues
+    lam = np.linalg.eigvalsh(W.dense("A"))
+    assert np.all(np.sort(theta) >= lam[: len(theta)] - 1e-9)
+    basis.close()
+    op.close()
+
+
+def test_incremental_and_initcg_parity_fp64(api, small):
+    """Sec. 4 box on 4 RHS, then batched init-CG (k = 4) with the restart of Sec. 5.3."""
+    dims, m_q, gauge, W, bs = small
+    op = api.Op(gauge, dims, m_q, prec=64, max_rhs=4)
+    basis = api.Basis(op, 64)
+    U0, H0, ores = solvers.incremental_eigcg(W, bs[:4], nev=8, m=24, tol=1e-10)
+    for r in range(4):
+        x = np.zeros_like(bs[r])
+        st = op.eigcg_solve(bs[r], x, nev=8, m=24, tol=1e-10, basis=basis)
+        assert _close_iters(st["iters"], ores[r]["iters"]), (r, st["iters"], ores[r]["iters"])
+        assert _true_res(W, x, bs[r]) <= 1e-10
+        basis.grow()
+    assert basis.size == U0.shape[1]
+    # basis invariants on the GPU's own vectors
+    U = basis.vectors()
+    H = basis.H()
+    l = U.shape[1]
+    assert np.max(np.abs(U.conj().T @ U - np.eye(l))) < 1e-10
+    AU = np.stack([W.A(U[:, c]) for c in range(l)], axis=1)
+    assert np.max(np.abs(H - U.conj().T @ AU)) < 1e-10 * 64
+    # converged Ritz values agree with the oracle's Rayleigh-Ritz on its own basis
+    th_g, rn_g = basis.ritz()
+    th_o, rn_o, _ = solvers.basis_ritz(W, U0, H0)
+    conv = rn_o < 1e-8
+    assert conv.sum() >= 4
+    assert np.all(np.abs(th_g[conv] - th_o[conv]) / th_o[conv] < 1e-6)
+    # init-CG, 4 RHS in one batch, restarted once at 1e-5
+    B = np.stack(bs[4:8])
+    X = np.zeros_like(B)
+    sts = op.initcg_solve(B, X, tol=1e-10, restart_tol=1e-5, basis=basis, k=4)
+    for r in range(4):
+        o = solvers.initcg(W, U, H, bs[4 + r], tol=1e-10, restart_tol=1e-5)
+        assert sts[r]["restarts"] == 1
+        assert _close_iters(sts[r]["iters"], o["iters"], 0.15), (r, sts[r]["iters"], o["iters"])
+        assert _true_res(W, X[r], bs[4 + r]) <= 1e-10
+    plain = solvers.cg(W, bs[4], tol=1e-10)
+    assert sts[0]["iters"] < plain["iters"]
+    basis.close()
+    op.close()
+
+
+def test_deflate_galerkin_and_parity(api, small):
+    dims, m_q, gauge, W, bs = small
+    op = api.Op(gauge, dims, m_q, prec=64, max_rhs=2)
+    basis = api.Basis(op, 32)
+    for r in range(2):
+        x = np.zeros_like(bs[r])
+        op.eigcg_solve(bs[r], x, nev=8, m=24, tol=1e-10, basis=basis)
+        basis.grow()
+    U, H = basis.vectors(), basis.H()
+    xt = fx.make_rhs(dims, 4242, 2)
+    B = np.stack(bs[2:4])
+    X0 = np.zeros_like(B)
+    basis.deflate(B, xt.reshape(2, -1).copy(), X0, k=2)
+    for r in range(2):
+        g = U.conj().T @ (B[r] - W.A(X0[r]))
+        assert np.linalg.norm(g) < 1e-11 * np.linalg.norm(B[r])
+        ref = solvers.deflated_guess(W, U, H, B[r], xt[r].reshape(-1))
+        assert np.linalg.norm(X0[r] - ref) / np.linalg.norm(ref) < 1e-10
+    basis.close()
+    op.close()
+
+
+@pytest.mark.parametrize("prec,frac", [(32, 0.10), (16, 0.35)])
+def test_mixed_precision_reaches_1e8(api, prec, frac):
+    """8^4, cond ~ 1e4: FP32 / FP16 storage with FP64 reliable updates reach 1e-8."""
+    dims = fx.LATTICES["8^4"]
+    m_q = MASSES["8^4"]["1e+04"]["m_q"]
+    gauge = fx.make_gauge(dims, fx.GAUGE_SEEDS["8^4"])
+    W = oracle.Wilson(dims, m_q, gauge)
+    b = fx.make_rhs(dims, fx.rhs_seed("8^4", 0))[0].reshape(-1)
+    op = api.Op(gauge, dims, m_q, prec=prec)
+    x = np.zeros_like(b)
+    st = op.initcg_solve(b, x, tol=1e-8)[0]
+    o = solvers.cg(W, b, tol=1e-8)
+    assert _true_res(W, x, b) <= 1e-8
+    assert st["reliable_updates"] >= 1
+    assert _close_iters(st["iters"], o["iters"], frac), (st["iters"], o["iters"])
+    # eigCG in mixed precision: same residual bar, Ritz values near the FP64 ones
+    basis = api.Basis(op, 16)
+    x2 = np.zeros_like(b)
+    st2 = op.eigcg_solve(b, x2, nev=8, m=40, tol=1e-8, basis=basis)
+    assert _true_res(W, x2, b) <= 1e-8
+    basis.grow()
+    th, rn = basis.ritz()
+    oe = solvers.eigcg(W, b, nev=8, m=40, tol=1e-8)
+    assert abs(th[0] - oe["ritz"][0]) / oe["ritz"][0] < (1e-4 if prec == 32 else 1e-2)
+    op.close()
+
+
+def test_batched_equals_alone(api, small):
+    """Each RHS gives the same solution alone and inside a batch of 4."""
+    dims, m_q, gauge, W, bs = small
+    op = api.Op(gauge, dims, m_q, prec=32, max_rhs=4)
+    B = np.stack(bs[:4])
+    X = np.zeros_like(B)
+    sts = op.initcg_solve(B, X, tol=1e-9, k=4)
+    for r in range(4):
+        x1 = np.zeros_like(bs[r])
+        s1 = op.initcg_solve(bs[r], x1, tol=1e-9, k=1)[0]
+        assert np.linalg.norm(X[r] - x1) / np.linalg.norm(x1) < 1e-6
+        assert s1["iters"] == sts[r]["iters"]
+    op.close()
+
+
+def test_edge_cases(api, small):
+    from paper_0707_0131_gb300 import _lib
+
+    dims, m_q, gauge, W, bs = small
+    op = api.Op(gauge, dims, m_q, prec=64)
+    # zero right-hand side: solution 0 in zero iterations
+    z = np.zeros_like(bs[0])
+    x = np.zeros_like(z)
+    st = op.initcg_solve(z, x, tol=1e-10)[0]
+    assert st["iters"] == 0 and np.all(x == 0)
+    # exact initial guess: zero iterations
+    o = solvers.cg(W, bs[0], tol=1e-13)
+    x = o["x"].copy()
+    st = op.initcg_solve(bs[0], x, tol=1e-10)[0]
+    assert st["iters"] == 0
+    # eigCG on a zero RHS leaves no Ritz pairs
+    basis = api.Basis(op, 8)
+    x = np.zeros_like(z)
+    st = op.eigcg_solve(z, x, nev=2, m=8, tol=1e-10, basis=basis)
+    assert st["iters"] == 0 and st["n_ritz"] == 0
+    # max_iter reached -> warning status, x is the last iterate
+    x = np.zeros_like(z)
+    st = op.initcg_solve(bs[0], x, tol=1e-12, max_iter=5)[0]
+    assert st["status"] == _lib.EIG_NOT_CONVERGED
+    # argument errors
+    with pytest.raises(_lib.EigError):
+        op.eigcg_solve(bs[0], x, nev=8, m=16, tol=1e-10)  # m <= 2 nev
+    with pytest.raises(_lib.EigError):
+        op.initcg_solve(bs[0], x, tol=1e-10, k=2)  # k > max_rhs
+    # smallest window: m = 2 nev + 1 restarts every iteration after the first fill
+    basis2 = api.Basis(op, 8)
+    x = np.zeros_like(z)
+    st = op.eigcg_solve(bs[0], x, nev=2, m=5, tol=1e-10, basis=basis2)
+    assert _true_res(W, x, bs[0]) <= 1e-10 and st["restarts"] > 10
+    o = solvers.eigcg(W, bs[0], nev=2, m=5, tol=1e-10)
+    basis2.grow()
+    th, _ = basis2.ritz(residuals=False)
+    assert abs(th[0] - o["ritz"][0]) / o["ritz"][0] < 1e-6
+    op.close()
