@@ -58,6 +58,11 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--mode", default="solve", choices=["solve", "dslash"],
+                    help="dslash: only repeated matvecs through eig_op_apply (kernel GB/s)")
+    ap.add_argument("--prec", type=int, default=32)
+    ap.add_argument("--which", type=int, default=2, help="dslash mode: 0 M, 1 M^H, 2 A")
+    ap.add_argument("--reps", type=int, default=20)
     return ap.parse_args()
 
 
@@ -173,10 +178,47 @@ def run_reference(a):
     print(json.dumps(out), flush=True)
 
 
+def run_dslash(a):
+    """Repeated matvecs on device-resident fields: per-kernel launches, time and GB/s."""
+    import torch
+
+    from paper_0707_0131_gb300 import _lib
+    from paper_0707_0131_gb300.api import Op
+
+    torch.cuda.set_device(0)
+    dims = fx.LATTICES[a.lattice]
+    m_q, _ = mass_for(a.lattice, a.kappa)
+    gauge = fx.make_gauge(dims, fx.GAUGE_SEEDS[a.lattice])
+    op = Op(gauge, dims, m_q, prec=a.prec, max_rhs=a.k)
+    x = torch.from_numpy(fx.make_rhs(dims, 7, a.k)).cuda()
+    y = torch.empty_like(x)
+    for _ in range(3):
+        op.apply(a.which, x, y, a.k)
+    _lib.eig_profile_reset()
+    _lib.eig_profile_enable(True)
+    for _ in range(a.reps):
+        op.apply(a.which, x, y, a.k)
+    _lib.eig_profile_enable(False)
+    prof = _lib.eig_profile_read()
+    peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"] \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
+    out = {"mode": "dslash", "lattice": a.lattice, "k": a.k, "prec": a.prec, "which": a.which, "kernels": {}}
+    for n, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"]):
+        gbs = v["bytes"] / (v["ms"] / 1e3) / 1e9 if v["ms"] > 0 else None
+        out["kernels"][n] = {"launches": v["launches"], "ms_per_launch": v["ms"] / max(1, v["launches"]),
+                             "GBps": gbs, "frac_of_hbm": gbs / peak if gbs else None,
+                             "bytes_per_launch": v["bytes"] / max(1, v["launches"])}
+    print(json.dumps(out), flush=True)
+    op.close()
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+        return
+    if a.mode == "dslash":
+        run_dslash(a)
         return
     import torch
 
@@ -204,7 +246,7 @@ def main():
     gauge = fx.make_gauge(dims, fx.GAUGE_SEEDS[a.lattice])
     k = a.k
     op = Op(gauge, dims, m_q, prec=32, max_rhs=k)
-    basis = Basis(op, max(a.basis, 16))
+    basis = Basis(op, a.basis + a.nev)
     nrhs_id = [0]
 
     def next_rhs(n):

@@ -631,6 +631,37 @@ static ColSet field_cols(void *base, bool f64, int k, long fsize, int ncols, boo
     return c;
 }
 
+// Gram-Schmidt in coefficient space: given the Gram matrix G (n x n row-major) of n
+// vectors, returns Rinv (column c = coefficients of kept orthonormal vector c, n x r
+// column-major) and the kept original indices; vectors whose remainder norm is
+// <= drop are skipped.  Two projection passes per vector.
+static void gram_orth(const std::vector<cd> &G, int n, double drop, std::vector<cd> &Rinv, std::vector<int> &keep) {
+    Rinv.assign((size_t)n * n, cd(0.0));
+    keep.clear();
+    auto gdot = [&](const cd *u, const cd *v) {
+        cd acc = 0.0;
+        for (int a = 0; a < n; a++)
+            for (int b = 0; b < n; b++) acc += std::conj(u[a]) * G[(size_t)a * n + b] * v[b];
+        return acc;
+    };
+    std::vector<cd> v(n);
+    for (int c = 0; c < n; c++) {
+        std::fill(v.begin(), v.end(), cd(0.0));
+        v[c] = 1.0;
+        for (int pass = 0; pass < 2; pass++)
+            for (int q = 0; q < (int)keep.size(); q++) {
+                const cd *u = &Rinv[(size_t)q * n];
+                const cd d = gdot(u, v.data());
+                for (int a = 0; a < n; a++) v[a] -= d * u[a];
+            }
+        const double nv = std::sqrt(std::max(0.0, gdot(v.data(), v.data()).real()));
+        if (!(nv > drop)) continue;
+        const int q = (int)keep.size();
+        for (int a = 0; a < n; a++) Rinv[(size_t)q * n + a] = v[a] / nv;
+        keep.push_back(c);
+    }
+}
+
 static void refactor(eig_basis_s *B) {
     const int l = B->l;
     B->Lc = B->H;
@@ -1008,31 +1039,10 @@ eig_status eig_basis_grow(eig_basis B, void *stream) {
     CUDA_CK(cudaMemcpyAsync(B->Ch.p, B->C.p, (size_t)np * np * 16, cudaMemcpyDeviceToHost, s));
     sync(s);
     std::vector<cd> G(B->Ch.as<cd>(), B->Ch.as<cd>() + (size_t)np * np);
-    // Gram-Schmidt in coefficient space: columns of R^{-1} for the kept vectors
     const double drop = f64 ? 1e-10 : 1e-4;
-    std::vector<cd> Rinv((size_t)np * np, cd(0.0));  // column c: coefficients of kept vector c
+    std::vector<cd> Rinv;
     std::vector<int> keep;
-    for (int c = 0; c < np; c++) {
-        // coefficient vector e_c projected against kept ones (in the G inner product), twice
-        std::vector<cd> v(np, cd(0.0));
-        v[c] = 1.0;
-        for (int pass = 0; pass < 2; pass++)
-            for (int q = 0; q < (int)keep.size(); q++) {
-                const cd *u = &Rinv[(size_t)q * np];
-                cd dot = 0.0;  // u^H G v
-                for (int a = 0; a < np; a++)
-                    for (int bb = 0; bb < np; bb++) dot += std::conj(u[a]) * G[(size_t)a * np + bb] * v[bb];
-                for (int a = 0; a < np; a++) v[a] -= dot * u[a];
-            }
-        cd nn = 0.0;
-        for (int a = 0; a < np; a++)
-            for (int bb = 0; bb < np; bb++) nn += std::conj(v[a]) * G[(size_t)a * np + bb] * v[bb];
-        const double nv = std::sqrt(std::max(0.0, nn.real()));
-        if (nv <= drop) continue;
-        const int q = (int)keep.size();
-        for (int a = 0; a < np; a++) Rinv[(size_t)q * np + a] = v[a] / nv;
-        keep.push_back(c);
-    }
+    gram_orth(G, np, drop, Rinv, keep);
     const int r = (int)keep.size();
     if (r == 0) {
         B->npend = 0;
@@ -1049,6 +1059,30 @@ eig_status eig_basis_grow(eig_basis B, void *stream) {
     B->Y.ensure(yr.size() * sizeof(double));
     CUDA_CK(cudaMemcpyAsync(B->Y.p, yr.data(), yr.size() * sizeof(double), cudaMemcpyHostToDevice, s));
     CUDA_CK(launch_gemm_ay(P, B->Y.as<double>(), basis_cols(B, l, r), 0.0, nrow, s));
+    {
+        // second pass: the remainders can be nearly dependent, so orthonormalise again
+        ColSet Un = basis_cols(B, l, r);
+        CUDA_CK(launch_gemm_ahb(Un, Un, nrow, B->C.as<double>(), op->red(), s));
+        CUDA_CK(cudaMemcpyAsync(B->Ch.p, B->C.p, (size_t)r * r * 16, cudaMemcpyDeviceToHost, s));
+        sync(s);
+        std::vector<cd> G2(B->Ch.as<cd>(), B->Ch.as<cd>() + (size_t)r * r);
+        std::vector<cd> R2;
+        std::vector<int> keep2;
+        gram_orth(G2, r, 0.0, R2, keep2);
+        if ((int)keep2.size() != r) throw Error{EIG_ERR_BREAKDOWN, "basis re-orthonormalisation lost rank"};
+        std::vector<double> y2((size_t)r * r * 2);
+        for (int a = 0; a < r; a++)
+            for (int c = 0; c < r; c++) {
+                y2[((size_t)a * r + c) * 2] = R2[(size_t)c * r + a].real();
+                y2[((size_t)a * r + c) * 2 + 1] = R2[(size_t)c * r + a].imag();
+            }
+        CUDA_CK(cudaMemcpyAsync(B->Y.p, y2.data(), y2.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+        CUDA_CK(launch_gemm_ay(Un, B->Y.as<double>(), field_cols(B->pend.p, f64, 1, B->fsize(), r, false), 0.0,
+                               nrow, s));
+        CUDA_CK(cudaMemcpyAsync((char *)B->U.p + (size_t)l * op->wfield_bytes(), B->pend.p,
+                                (size_t)r * op->wfield_bytes(), cudaMemcpyDeviceToDevice, s));
+        sync(s);
+    }
     // W = A V-bar with the FP64 operator, stored in window precision
     Field x64 = op->x64.view(1), r64f = op->b64.view(1);
     for (int c = 0; c < r; c++) {
