@@ -204,13 +204,18 @@ struct eig_op_s {
         h.cap = hist_cap;
         return h;
     }
+    // The history layout depends on k (three arrays of cap * k doubles); the
+    // allocation is tracked in doubles per array so that a later solve with more
+    // RHS than an earlier one reallocates.
+    size_t hist_elems = 0;
     void ensure_history(int iters, int k) {
-        const int need = iters + 4;
-        if (need * k > hist_cap * k || hist_cap < need) {
-            hist.alloc((size_t)need * k * 3 * sizeof(double));
-            hist_cap = need;
+        hist_cap = iters + 4;
+        const size_t need = (size_t)hist_cap * k;
+        if (need > hist_elems) {
+            hist.alloc(need * 3 * sizeof(double));
+            hist_elems = need;
         }
-        hist_h.ensure((size_t)hist_cap * k * 3 * sizeof(double));
+        hist_h.ensure(need * 3 * sizeof(double));
     }
 };
 

@@ -134,12 +134,14 @@ def test_incremental_and_initcg_parity_fp64(api, small):
     assert np.max(np.abs(U.conj().T @ U - np.eye(l))) < 1e-10
     AU = np.stack([W.A(U[:, c]) for c in range(l)], axis=1)
     assert np.max(np.abs(H - U.conj().T @ AU)) < 1e-10 * 64
-    # converged Ritz values agree with the oracle's Rayleigh-Ritz on its own basis
+    # Rayleigh-Ritz on the GPU basis against the oracle's on its own basis; the bottom
+    # of this spectrum is clustered, so compare to the accuracy each run determines
     th_g, rn_g = basis.ritz()
     th_o, rn_o, _ = solvers.basis_ritz(W, U0, H0)
-    conv = rn_o < 1e-8
-    assert conv.sum() >= 4
-    assert np.all(np.abs(th_g[conv] - th_o[conv]) / th_o[conv] < 1e-6)
+    rel = np.abs(th_g[:8] - th_o[:8]) / th_o[:8]
+    assert np.all(rel[:2] < 1e-6) and np.all(rel < 1e-4), (rel, rn_o[:8])
+    lam = np.linalg.eigvalsh(W.dense("A"))
+    assert np.all(th_g >= lam[: len(th_g)] - 1e-9)
     # init-CG, 4 RHS in one batch, restarted once at 1e-5
     B = np.stack(bs[4:8])
     X = np.zeros_like(B)
@@ -202,7 +204,12 @@ def test_mixed_precision_reaches_1e8(api, prec, frac):
     basis.grow()
     th, rn = basis.ritz()
     oe = solvers.eigcg(W, b, nev=8, m=40, tol=1e-8)
-    assert abs(th[0] - oe["ritz"][0]) / oe["ritz"][0] < (1e-4 if prec == 32 else 1e-2)
+    # FP32: relative 1e-4; FP16 Lanczos vectors resolve eigenvalues only to a small
+    # multiple of eps_16 ||A|| (||A|| ~ 64 here), so its bar is absolute
+    if prec == 32:
+        assert abs(th[0] - oe["ritz"][0]) / oe["ritz"][0] < 1e-4
+    else:
+        assert abs(th[0] - oe["ritz"][0]) < 1e-5 * 64
     op.close()
 
 
