@@ -58,8 +58,13 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--mode", default="solve", choices=["solve", "dslash"],
-                    help="dslash: only repeated matvecs through eig_op_apply (kernel GB/s)")
+    ap.add_argument("--mode", default="solve", choices=["solve", "dslash", "serve"],
+                    help="dslash: only repeated matvecs through eig_op_apply (kernel GB/s); "
+                         "serve: Poisson requests over 9 operators through the serving loop")
+    ap.add_argument("--requests", type=int, default=200, help="serve mode: number of requests")
+    ap.add_argument("--serve-lattices", default="8^4,16^3x32,24^3x64")
+    ap.add_argument("--serve-basis", type=int, default=40)
+    ap.add_argument("--budget-gb", type=float, default=150.0)
     ap.add_argument("--prec", type=int, default=32)
     ap.add_argument("--which", type=int, default=2, help="dslash mode: 0 M, 1 M^H, 2 A")
     ap.add_argument("--reps", type=int, default=20)
@@ -212,8 +217,90 @@ def run_dslash(a):
     op.close()
 
 
+def run_serve(a):
+    """Serving form: Poisson-arriving single-RHS requests over 3 lattices x 3 masses,
+    continuous batching with per-operator resident bases under an HBM budget."""
+    import torch
+
+    from paper_0707_0131_gb300 import serving
+    from paper_0707_0131_gb300.api import Op
+
+    torch.cuda.set_device(0)
+    specs = []
+    for name in a.serve_lattices.split(","):
+        dims = fx.LATTICES[name]
+        gauge = fx.make_gauge(dims, fx.GAUGE_SEEDS[name])
+        for kappa in ("1e+03", "1e+04", "1e+05"):
+            m_q, _ = mass_for(name, kappa)
+            specs.append(serving.OpSpec(key=f"{name}/{kappa}", dims=dims, m_q=m_q, gauge=gauge, prec=32,
+                                        max_rhs=a.k, nev=a.nev, m=a.m, basis_max=a.serve_basis, tol=a.tol,
+                                        restart_tol=a.restart_tol))
+    by_key = {s.key: s for s in specs}
+    rng = np.random.default_rng(105)
+    keys = [specs[i].key for i in rng.integers(0, len(specs), size=a.requests)]
+    rhs_cache = {}
+
+    def rhs(i):
+        key = keys[i]
+        if key not in rhs_cache:
+            rhs_cache[key] = [fx.make_rhs(by_key[key].dims, 4_000_000 + j)[0].reshape(-1) for j in range(8)]
+        return rhs_cache[key][i % 8]
+
+    # plain FP64 eigCG per request (same GPU, no deflation, no batching): one solve per operator
+    plain_ms = {}
+    if not a.no_plain:
+        for s_ in specs:
+            op64 = Op(s_.gauge, s_.dims, s_.m_q, prec=64)
+            b = torch.from_numpy(rhs_cache.setdefault(s_.key, [fx.make_rhs(s_.dims, 4_000_000 + j)[0].reshape(-1)
+                                                               for j in range(8)])[0]).cuda()
+            x = torch.zeros_like(b)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            op64.eigcg_solve(b, x, s_.nev, s_.m, s_.tol, max_iter=50000)
+            torch.cuda.synchronize()
+            plain_ms[s_.key] = (time.perf_counter() - t0) * 1e3
+            op64.close()
+    # capacity: one closed-loop pass of len(specs) * 2 requests
+    srv = serving.Server(specs, hbm_budget_bytes=a.budget_gb * 1e9)
+    t0 = time.perf_counter()
+    warm = [srv.submit(s_.key, rhs_cache.setdefault(s_.key, [fx.make_rhs(s_.dims, 4_000_000 + j)[0].reshape(-1)
+                                                              for j in range(8)])[j])
+            for j in range(2) for s_ in specs]
+    for f in warm:
+        f.result()
+    cap = len(warm) / (time.perf_counter() - t0)
+    rate = 0.8 * cap
+    srv.latencies.clear()
+    arrivals = serving.poisson_arrivals(rate, a.requests, 105)
+    futs = []
+    t0 = time.perf_counter()
+    for i, ta in enumerate(arrivals):
+        now = time.perf_counter() - t0
+        if ta > now:
+            time.sleep(ta - now)
+        futs.append((keys[i], srv.submit(keys[i], rhs(i))))
+    res = [(k_, f.result()) for k_, f in futs]
+    wall = time.perf_counter() - t0
+    pct = srv.percentiles()
+    plain_mean = float(np.mean([plain_ms[k_] for k_, _ in res])) if plain_ms else None
+    out = {"mode": "serve", "metric": "RHS/s and latency under Poisson load", "value": len(res) / wall,
+           "unit": UNIT, "p50_ms": pct["p50_ms"], "p99_ms": pct["p99_ms"], "requests": len(res),
+           "arrival_rate_per_s": rate, "capacity_estimate_per_s": cap,
+           "plain_fp64_eigcg_ms_per_request_mean": plain_mean,
+           "max_true_rel_res": float(max(r["stats"]["true_rel_res"] for _, r in res)),
+           "batched_fraction": float(np.mean([r["batch"] > 1 for _, r in res])),
+           "max_hbm_used_gb": srv.max_used / 1e9, "budget_gb": a.budget_gb,
+           "config": {"workload": f"{len(specs)} operators ({a.serve_lattices} x cond 1e3/1e4/1e5), basis "
+                                  f"{a.serve_basis}, eigCG({a.nev},{a.m}) then init-CG batches of <= {a.k}, tol {a.tol}"}}
+    srv.close()
+    print(json.dumps(out), flush=True)
+
+
 def main():
     a = parse()
+    if a.mode == "serve":
+        run_serve(a)
+        return
     if a.impl == "reference":
         run_reference(a)
         return

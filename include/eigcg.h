@@ -89,7 +89,9 @@ eig_status eig_op_create(const double *gauge, const int dims[4], double m_q, con
 eig_status eig_op_destroy(eig_op op);
 
 /* out = M in (which 0), M^H in (which 1) or A in (which 2) for k RHS (1..max_rhs),
- * in the op's storage precision.  in/out: natural layout, may alias.
+ * in the op's storage precision; which 3 (FP32/FP16 ops only) applies A in the
+ * double-float arithmetic of the residual replacements (about 44-bit precision).
+ * in/out: natural layout, may alias.
  * This is the dslash of the CG matrix-vector product (Fig. 1 step 11). */
 eig_status eig_op_apply(eig_op op, int which, const double *in, double *out, int k, void *stream);
 

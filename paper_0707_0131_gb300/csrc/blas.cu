@@ -256,10 +256,12 @@ cudaError_t launch_norm2(Field f, CGScalars *st, bool as_rho, History h, int ite
 }
 
 // ---------------------------------------------------------------------------------------
-// p = r + beta p  (+ window append v = r / sqrt(rho))
+// x += alpha p (pending from the previous iteration), p = r + beta p, window append
+// v = r / sqrt(rho).  x lives in the wide precision (FP64 for FP64 storage, else FP32).
 // ---------------------------------------------------------------------------------------
 template <typename S, typename SV>
-__global__ void k_pupdate(FieldView r, FieldView p, int first, const CGScalars *st, FieldView v, int append) {
+__global__ void k_pupdate(FieldView r, FieldView p, FieldView x, int first, const CGScalars *st, FieldView v,
+                          int append) {
     using C = typename SpinorStore<S>::C;
     using CV = typename SpinorStore<SV>::C;
     {
@@ -277,8 +279,21 @@ __global__ void k_pupdate(FieldView r, FieldView p, int first, const CGScalars *
         if (first) {
             pp = rr;
         } else {
-            const C be = sc.active ? (C)sc.beta : (C)0;
             SpinorStore<S>::load(p, s, q, pp);
+            if (sc.x_pending) {  // Fig. 1 step 13 of the previous iteration
+                const CV al = (CV)sc.alpha;
+                Spinor<CV> xx;
+                SpinorStore<SV>::load(x, s, q, xx);
+#pragma unroll
+                for (int i = 0; i < 4; i++)
+#pragma unroll
+                    for (int j = 0; j < 3; j++) {
+                        xx.s[i][j].re += al * (CV)pp.s[i][j].re;
+                        xx.s[i][j].im += al * (CV)pp.s[i][j].im;
+                    }
+                SpinorStore<SV>::store(x, s, q, xx);
+            }
+            const C be = sc.active ? (C)sc.beta : (C)0;
 #pragma unroll
             for (int i = 0; i < 4; i++)
 #pragma unroll
@@ -298,28 +313,69 @@ __global__ void k_pupdate(FieldView r, FieldView p, int first, const CGScalars *
     }
 }
 
-cudaError_t launch_pupdate(Field r, Field p, bool first, CGScalars *st, Field v_append, cudaStream_t s) {
-    ProfScope prof("pupdate", (double)r.v.V * r.v.k * ((first ? 2.0 : 3.0) * spb(r.prec)) +
-                                  (v_append.v.data ? (double)r.v.V * spb(v_append.prec) : 0.0), s);
+cudaError_t launch_pupdate(Field r, Field p, Field x, bool first, CGScalars *st, Field v_append, cudaStream_t s) {
+    const int app = v_append.v.data != nullptr;
+    ProfScope prof("pupdate", (double)r.v.V * r.v.k * ((first ? 2.0 : 3.0) * spb(r.prec) + (first ? 0.0 : 2.0 * spb(x.prec))) +
+                                  (app ? (double)r.v.V * spb(v_append.prec) : 0.0), s);
     const int B = 128;
     const int G = stream_grid(r.v.V * r.v.k, B);
-    const int app = v_append.v.data != nullptr;
-    if (app && v_append.prec == P16) return cudaErrorInvalidValue;
-    const bool v64 = app && v_append.prec == P64;
+    if (app && v_append.prec != x.prec) return cudaErrorInvalidValue;
     switch (r.prec) {
         case P64:
-            if (app && !v64) return cudaErrorInvalidValue;
-            k_pupdate<double, double><<<G, B, 0, s>>>(r.v, p.v, first, st, v_append.v, app);
+            if (x.prec != P64) return cudaErrorInvalidValue;
+            k_pupdate<double, double><<<G, B, 0, s>>>(r.v, p.v, x.v, first, st, v_append.v, app);
             break;
         case P32:
-            if (v64) return cudaErrorInvalidValue;
-            k_pupdate<float, float><<<G, B, 0, s>>>(r.v, p.v, first, st, v_append.v, app);
+            if (x.prec != P32) return cudaErrorInvalidValue;
+            k_pupdate<float, float><<<G, B, 0, s>>>(r.v, p.v, x.v, first, st, v_append.v, app);
             break;
         case P16:
-            if (v64) return cudaErrorInvalidValue;
-            k_pupdate<__half, float><<<G, B, 0, s>>>(r.v, p.v, first, st, v_append.v, app);
+            if (x.prec != P32) return cudaErrorInvalidValue;
+            k_pupdate<__half, float><<<G, B, 0, s>>>(r.v, p.v, x.v, first, st, v_append.v, app);
             break;
     }
+    return cudaGetLastError();
+}
+
+template <typename S, typename SV>
+__global__ void k_xflush(FieldView p, FieldView x, const CGScalars *st) {
+    using C = typename SpinorStore<S>::C;
+    using CV = typename SpinorStore<SV>::C;
+    const long total = p.V * p.k;
+    for (long g = (long)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += (long)gridDim.x * blockDim.x) {
+        const long s = g / p.k;
+        const int q = (int)(g - s * p.k);
+        if (!st[q].x_pending) continue;
+        const CV al = (CV)st[q].alpha;
+        Spinor<C> pp;
+        Spinor<CV> xx;
+        SpinorStore<S>::load(p, s, q, pp);
+        SpinorStore<SV>::load(x, s, q, xx);
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                xx.s[i][j].re += al * (CV)pp.s[i][j].re;
+                xx.s[i][j].im += al * (CV)pp.s[i][j].im;
+            }
+        SpinorStore<SV>::store(x, s, q, xx);
+    }
+}
+
+__global__ void k_clear_pending(CGScalars *st, int k) {
+    if (threadIdx.x < k) st[threadIdx.x].x_pending = 0;
+}
+
+cudaError_t launch_xflush(Field p, Field x, CGScalars *st, int k, cudaStream_t s) {
+    ProfScope prof("xflush", (double)p.v.V * p.v.k * (spb(p.prec) + 2.0 * spb(x.prec)), s);
+    const int B = 128;
+    const int G = stream_grid(p.v.V * p.v.k, B);
+    switch (p.prec) {
+        case P64: k_xflush<double, double><<<G, B, 0, s>>>(p.v, x.v, st); break;
+        case P32: k_xflush<float, float><<<G, B, 0, s>>>(p.v, x.v, st); break;
+        case P16: k_xflush<__half, float><<<G, B, 0, s>>>(p.v, x.v, st); break;
+    }
+    k_clear_pending<<<1, 32, 0, s>>>(st, k);
     return cudaGetLastError();
 }
 
@@ -333,6 +389,7 @@ __global__ void k_cg_init(CGScalars *st, int k, double tol2, double *h_beta) {
     st[r].beta = 0.0;
     st[r].pAp = 0.0;
     st[r].iters = 0;
+    st[r].x_pending = 0;
     if (h_beta) h_beta[k + r] = 0.0;  // beta_1 := 0
 }
 

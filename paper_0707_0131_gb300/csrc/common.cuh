@@ -325,4 +325,26 @@ __device__ __forceinline__ void grid_reduce_rhs(double blocksum, int k, double *
     if (threadIdx.x == 0) *counter = 0u;
 }
 
+// As grid_reduce_rhs, for kernels whose blocks have already written their k
+// per-RHS partial sums to partials[blockIdx.x * k + r].
+template <typename F>
+__device__ __forceinline__ void grid_finish_rhs(int k, double *partials, unsigned *counter, double *smem, F finish) {
+    __shared__ bool am_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned prev = atomicAdd(counter, 1u);
+        am_last = (prev == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!am_last) return;
+    __threadfence();
+    const int r = threadIdx.x % k;
+    double s = 0.0;
+    for (long b = threadIdx.x / k; b < gridDim.x; b += blockDim.x / k) s += __ldcg(partials + b * k + r);
+    double tot = block_reduce_rhs(s, k, smem);
+    if (threadIdx.x < k) finish(threadIdx.x, tot);
+    if (threadIdx.x == 0) *counter = 0u;
+}
+
 }  // namespace eig

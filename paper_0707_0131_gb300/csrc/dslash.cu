@@ -222,24 +222,18 @@ __global__ void __launch_bounds__(128) k_dslash(const KArgs a) {
         if (EPI == EPI_PLAIN || EPI == EPI_NORM) {
             SpinorStore<S>::store(a.out, s, r, out);
             if (EPI == EPI_NORM) nrm += site_norm2(out);
-        } else if (EPI == EPI_CG) {
+        } else if (EPI == EPI_CG) {  // r -= alpha t
             const CGScalars &st = a.st[r];
             const C al = st.active ? (C)st.alpha : (C)0;
-            Spinor<C> p, rr;
-            Spinor<W> x;
-            SpinorStore<S>::load(a.p, s, r, p);
+            Spinor<C> rr;
             SpinorStore<S>::load(a.r, s, r, rr);
-            SpinorStore<W>::load(a.x, s, r, x);
 #pragma unroll
             for (int i = 0; i < 4; i++)
 #pragma unroll
                 for (int j = 0; j < 3; j++) {
-                    x.s[i][j].re += (W)(al * p.s[i][j].re);
-                    x.s[i][j].im += (W)(al * p.s[i][j].im);
                     rr.s[i][j].re -= al * out.s[i][j].re;
                     rr.s[i][j].im -= al * out.s[i][j].im;
                 }
-            SpinorStore<W>::store(a.x, s, r, x);
             SpinorStore<S>::store(a.r, s, r, rr);
             nrm += site_norm2(rr);
             if (a.save_t) {
@@ -281,8 +275,10 @@ __global__ void __launch_bounds__(128) k_dslash(const KArgs a) {
                     st.alpha = st.rho / tot;
                 }
                 h_alpha[hi] = st.alpha;
+                st.x_pending = st.active;
             } else {
                 st.alpha = 0.0;
+                st.x_pending = 0;
             }
         } else if (EPI == EPI_CG) {
             if (st.active) {
@@ -383,7 +379,7 @@ static double dslash_bytes(const DslashCall &c, const KArgs &a) {
     const double sp = c.in.prec == P64 ? 192 : (c.in.prec == P32 ? 96 : 52);
     const double w = c.in.prec == P64 ? 192 : 96;
     double per_rhs = 2 * sp;                                                 // in + out
-    if (EPI == EPI_CG) per_rhs = sp + sp + 2 * sp + 2 * w + (a.save_t ? w : 0);  // u, p, r rw, x rw, t
+    if (EPI == EPI_CG) per_rhs = sp + 2 * sp + (a.save_t ? w : 0);           // u, r rw, t
     if (EPI == EPI_RESID) per_rhs = 3 * sp;                                  // u, b, r
     return (double)c.V * (site_bytes_gauge(c.gformat) + c.k * per_rhs);
 }
@@ -432,6 +428,10 @@ static cudaError_t dispatch(const DslashCall &c, KArgs &a, int cap, cudaStream_t
 
 cudaError_t launch_dslash(const DslashCall &c, cudaStream_t s) {
     KArgs a = base_args(c);
+    if (c.in.prec != P64) {
+        ProfScope prof(dslash_name(EPI_PLAIN, c.in.prec), dslash_bytes<EPI_PLAIN>(c, a), s);
+        return launch_dslash32(c, s);
+    }
     return dispatch<EPI_PLAIN>(c, a, 0, s);
 }
 
@@ -445,14 +445,16 @@ cudaError_t launch_dslash_norm(const DslashCall &c, CGScalars *st, History h, in
     a.iter = iter;
     a.partials = red.partials;
     a.counter = red.counter;
+    if (c.in.prec != P64) {
+        ProfScope prof(dslash_name(EPI_NORM, c.in.prec), dslash_bytes<EPI_NORM>(c, a), s);
+        return launch_dslash32_norm(c, st, h, iter, red, s);
+    }
     return dispatch<EPI_NORM>(c, a, red.max_blocks, s);
 }
 
-cudaError_t launch_dslash_cg(const DslashCall &c, Field p, Field x, Field r, Field t_save, CGScalars *st, History h,
-                             int iter, RedScratch red, cudaStream_t s) {
+cudaError_t launch_dslash_cg(const DslashCall &c, Field r, Field t_save, CGScalars *st, History h, int iter,
+                             RedScratch red, cudaStream_t s) {
     KArgs a = base_args(c);
-    a.p = p.v;
-    a.x = x.v;
     a.r = r.v;
     a.tsave = t_save.v;
     a.save_t = t_save.v.data != nullptr;
@@ -463,6 +465,10 @@ cudaError_t launch_dslash_cg(const DslashCall &c, Field p, Field x, Field r, Fie
     a.iter = iter;
     a.partials = red.partials;
     a.counter = red.counter;
+    if (c.in.prec != P64) {
+        ProfScope prof(dslash_name(EPI_CG, c.in.prec), dslash_bytes<EPI_CG>(c, a), s);
+        return launch_dslash32_cg(c, r, t_save, st, h, iter, red, s);
+    }
     return dispatch<EPI_CG>(c, a, red.max_blocks, s);
 }
 

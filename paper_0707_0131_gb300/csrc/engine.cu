@@ -158,7 +158,7 @@ struct eig_op_s {
     int gf_inner;
     int max_rhs;
     double delta;
-    DevBuf gauge64, gauge_in;
+    DevBuf gauge64, gauge_in, gauge_dd;  // gauge_dd: double-float copy (mixed precision)
     // workspace
     FieldBuf r, p, u, xlo, b64, x64, r64, u64, rsv, xsv;
     DevBuf nat_in, nat_out;
@@ -371,14 +371,25 @@ struct Solve {
     const double *hb() const { return op->hist_h.as<double>() + (size_t)h.cap * k; }
     const double *hr() const { return op->hist_h.as<double>() + 2 * (size_t)h.cap * k; }
 
-    // r64 = b - A x64 (FP64); with set_rho the CG scalars take the true residual.
-    void true_residual(bool set_rho) {
+    // r64 = b - A x64; with set_rho the CG scalars take the true residual.  final:
+    // FP64 arithmetic (the reported residual); otherwise, in mixed precision, the
+    // double-float stencil (residual replacements between checks).
+    void true_residual(bool set_rho, bool final_check = true) {
+        CUDA_CK(launch_xflush(p, xlo, st, k, s));
         if (mixed) {
             CUDA_CK(launch_combine(x64, 1.0, x64, 1.0, xlo, s));
             zero_field(xlo, s);
         }
-        apply_M(op, x64, u64, false, true, s);
-        CUDA_CK(launch_dslash_resid(op->call(u64, r64, true, true), b64, r64, st, h, j, set_rho, red, s));
+        if (mixed && !final_check) {
+            const long n = op->V * 12 * (long)k;
+            CUDA_CK(launch_to_dd(x64.v.data, r64.v.data, n, s));  // r64 holds x in dd until overwritten
+            CUDA_CK(launch_dslash_dd(op->call(x64, u64, false, true), op->gauge_dd.p, r64.v.data, u64.v.data, s));
+            CUDA_CK(launch_dslash_dd_resid(op->call(u64, r64, true, true), op->gauge_dd.p, u64.v.data, b64, r64, st, h,
+                                           j, set_rho, red, s));
+        } else {
+            apply_M(op, x64, u64, false, true, s);
+            CUDA_CK(launch_dslash_resid(op->call(u64, r64, true, true), b64, r64, st, h, j, set_rho, red, s));
+        }
         if (mixed && set_rho) CUDA_CK(launch_combine(r, 1.0, r64, 0.0, null_field(), s));
     }
 
@@ -388,7 +399,7 @@ struct Solve {
         CUDA_CK(launch_norm2(b64, st, false, h, 0, red, s));
         CUDA_CK(launch_cg_init(st, k, tol, h, s));
         if (mixed) zero_field(xlo, s);
-        true_residual(false);
+        true_residual(false, false);
         if (mixed) CUDA_CK(launch_combine(r, 1.0, r64, 0.0, null_field(), s));
         CUDA_CK(launch_norm2(r64, st, true, h, 0, red, s));
         read_scalars();
@@ -425,7 +436,7 @@ struct Solve {
         return trig;
     }
     void reliable_update() {
-        true_residual(true);
+        true_residual(true, false);
         read_scalars();
         for (int q = 0; q < k; q++) {
             rmax[q] = std::sqrt(sth[q].rho);
@@ -495,7 +506,7 @@ static bool cg_run(Solve &sv, int max_iter, Window *w, eig_op_s *op) {
             w->freel.pop_back();
             vapp = field_at(op->wprec, (char *)op->win.p + (size_t)slot * op->wfield_bytes(), op->V, 1);
         }
-        CUDA_CK(launch_pupdate(sv.r, sv.p, j == 1, sv.st, vapp, s));
+        CUDA_CK(launch_pupdate(sv.r, sv.p, sv.xlo, j == 1, sv.st, vapp, s));
         CUDA_CK(launch_dslash_norm(op->call(sv.p, sv.u, false, op->prec == P64),
                                    sv.st, sv.h, j, sv.red, s));
         Field tsave = null_field();
@@ -506,8 +517,7 @@ static bool cg_run(Solve &sv, int max_iter, Window *w, eig_op_s *op) {
             if (restart_now) tsave = field_at(op->wprec, tc, op->V, 1);
             else if (becomes_full) tsave = field_at(op->wprec, tp, op->V, 1);
         }
-        CUDA_CK(launch_dslash_cg(op->call(sv.u, sv.u, true, op->prec == P64), sv.p, sv.xlo, sv.r, tsave, sv.st, sv.h,
-                                 j, sv.red, s));
+        CUDA_CK(launch_dslash_cg(op->call(sv.u, sv.u, true, op->prec == P64), sv.r, tsave, sv.st, sv.h, j, sv.red, s));
         if (w) {
             if (restart_now) {
                 // step 11.7 (V <- V QZ in place) fused with step 11.8 (w^H V)
@@ -583,7 +593,14 @@ static bool cg_finish(Solve &sv, int max_iter, Window *w, eig_op_s *op, int &ext
     return again;
 }
 
+// Picks the stencil variant for this k on the op's own buffers (once per op shape).
+static void tune_for(eig_op_s *op, int k, cudaStream_t s) {
+    if (op->prec == P64 || k < 2) return;
+    CUDA_CK(autotune_dslash32(op->call(op->p.view(k), op->u.view(k), false, false), s));
+}
+
 static Solve make_solve(eig_op_s *op, int k, cudaStream_t s, int max_iter) {
+    tune_for(op, k, s);
     Solve sv;
     sv.op = op;
     sv.s = s;
@@ -775,6 +792,9 @@ eig_status eig_op_create(const double *gauge, const int dims[4], double m_q, con
     ARG_CHECK(o.spinor_prec == 64 || o.spinor_prec == 32 || o.spinor_prec == 16, "spinor_prec must be 64, 32 or 16");
     ARG_CHECK(o.max_rhs >= 1 && o.max_rhs <= MAX_RHS && (o.max_rhs & (o.max_rhs - 1)) == 0,
               "max_rhs must be a power of two in [1, 16]");
+    // the FP32/FP16 stencil addresses fields and link planes with 32-bit offsets
+    ARG_CHECK((unsigned long long)V * o.max_rhs * 6ull < (1ull << 32) && 36ull * V < (1ull << 32),
+              "lattice volume times max_rhs too large for one op");
     std::unique_ptr<eig_op_s> op(new eig_op_s());
     for (int i = 0; i < 4; i++) op->L[i] = dims[i];
     op->V = V;
@@ -792,6 +812,8 @@ eig_status eig_op_create(const double *gauge, const int dims[4], double m_q, con
     op->gauge64.alloc((size_t)V * 4 * 9 * 16);
     CUDA_CK(launch_pack_gauge(stage.as<double>(), op->gauge64.p, GF_F64_18, V, 0));
     if (op->prec != P64) {
+        op->gauge_dd.alloc((size_t)V * 4 * 9 * 16);
+        CUDA_CK(launch_to_dd(op->gauge64.p, op->gauge_dd.p, V * 4 * 9, 0));
         size_t gb = op->gf_inner == GF_F32_12 ? 48 : (op->gf_inner == GF_F32_18 ? 72 : 24);
         op->gauge_in.alloc((size_t)V * 4 * gb);
         CUDA_CK(launch_pack_gauge(stage.as<double>(), op->gauge_in.p, op->gf_inner, V, 0));
@@ -834,12 +856,24 @@ eig_status eig_op_destroy(eig_op op) {
 eig_status eig_op_apply(eig_op op, int which, const double *in, double *out, int k, void *stream) {
     API_BEGIN
     ARG_CHECK(op && in && out, "null argument");
-    ARG_CHECK(which >= 0 && which <= 2, "which must be 0 (M), 1 (M^H) or 2 (A)");
+    ARG_CHECK(which >= 0 && which <= 3, "which must be 0 (M), 1 (M^H), 2 (A) or 3 (A in double-float)");
+    ARG_CHECK(which != 3 || op->prec != P64, "which = 3 needs an FP32 or FP16 op");
     ARG_CHECK(k >= 1 && k <= op->max_rhs && (k & (k - 1)) == 0, "k must be a power of two <= max_rhs");
     std::lock_guard<std::mutex> lk(op->mu);
     cudaStream_t s = (cudaStream_t)stream;
     Field x64 = op->x64.view(k);
     load_natural(op, in, x64, s);
+    if (which == 3) {  // A = M^H M in double-float arithmetic
+        const long n = op->V * 12 * (long)k;
+        Field t1 = op->u64.view(k), t2 = op->r64.view(k);
+        CUDA_CK(launch_to_dd(x64.v.data, t1.v.data, n, s));
+        CUDA_CK(launch_dslash_dd(op->call(x64, t2, false, true), op->gauge_dd.p, t1.v.data, t2.v.data, s));
+        CUDA_CK(launch_dslash_dd(op->call(x64, t1, true, true), op->gauge_dd.p, t2.v.data, t1.v.data, s));
+        CUDA_CK(launch_from_dd(t1.v.data, x64.v.data, n, s));
+        store_natural(op, x64, out, s);
+        sync(s);
+        return EIG_OK;
+    }
     Field a = op->p.view(k), b = op->u.view(k), c = op->r.view(k);
     CUDA_CK(launch_combine(a, 1.0, x64, 0.0, null_field(), s));
     const bool f64 = op->prec == P64;
@@ -943,7 +977,11 @@ eig_status eig_eigcg_solve(eig_op op, eig_basis basis, const double *b, double *
     bool ok = true;
     while (true) {
         ok = cg_run(sv, max_iter, &w, op);
-        if (!ok) break;
+        if (!ok) {
+            sv.true_residual(false);  // folds x_lo (and a pending alpha p) into x
+            sv.read_scalars();
+            break;
+        }
         if (!cg_finish(sv, max_iter, &w, op, rounds)) break;
     }
     // eigCG output: nev lowest Ritz pairs of the final window
@@ -1180,7 +1218,7 @@ eig_status eig_initcg_solve(eig_op op, eig_basis basis, const double *b, double 
         const int j1 = sv.j;
         std::vector<int> rel1 = sv.reliable;
         if (ok) {
-            sv.true_residual(false);  // x64 += x_lo; r64 = b - A x64
+            sv.true_residual(false, false);  // x64 += x_lo; r64 = b - A x64
             deflate_into(basis, sv.r64, sv.x64, s);
             restarts = 1;
             sv.start(tol);

@@ -29,6 +29,7 @@ struct CGScalars {
     double aux;       // last auxiliary reduction (true residual norm^2, norm of b, ...)
     int active;       // 1 while iterating
     int iters;        // last iteration in which this RHS was active
+    int x_pending;    // 1: x still lacks alpha * p of the last iteration (applied by the next p update)
     int breakdown;    // 1 if pAp <= 0, NaN or Inf was met
 };
 
@@ -69,15 +70,34 @@ cudaError_t launch_dslash(const DslashCall &c, cudaStream_t s);
 // CG pass 1: out = M in, pAp = ||out||^2, alpha = rho / pAp   (Fig. 1 steps 11-12)
 cudaError_t launch_dslash_norm(const DslashCall &c, CGScalars *st, History h, int iter, RedScratch red,
                                cudaStream_t s);
-// CG pass 2: t = M^H in; x += alpha p; r -= alpha t; rho_new = ||r||^2; beta = rho_new / rho
-// (Fig. 1 steps 11-14 and 4/8 of the next iteration).  If t_save.v.data != nullptr, t is
-// also written there (window precision).
-cudaError_t launch_dslash_cg(const DslashCall &c, Field p, Field x, Field r, Field t_save, CGScalars *st, History h,
-                             int iter, RedScratch red, cudaStream_t s);
+// CG pass 2: t = M^H in; r -= alpha t; rho_new = ||r||^2; beta = rho_new / rho
+// (Fig. 1 steps 11, 14 and 4/8 of the next iteration).  Step 13 (x += alpha p) is
+// applied one iteration late by launch_pupdate, which reads p anyway.  If
+// t_save.v.data != nullptr, t is also written there (window precision).
+cudaError_t launch_dslash_cg(const DslashCall &c, Field r, Field t_save, CGScalars *st, History h, int iter,
+                             RedScratch red, cudaStream_t s);
 // FP64 residual: r = b - M^H in, aux = ||r||^2 (with set_rho: rho = aux, beta = rho / rho_prev,
 // history beta[iter + 1] = beta, rho[iter] = rho).
 cudaError_t launch_dslash_resid(const DslashCall &c, Field b, Field r, CGScalars *st, History h, int iter,
                                 bool set_rho, RedScratch red, cudaStream_t s);
+
+// dslash32.cu: FP32-arithmetic versions (FP32 / FP16 storage) of the three launches above
+cudaError_t launch_dslash32(const DslashCall &c, cudaStream_t s);
+cudaError_t launch_dslash32_norm(const DslashCall &c, CGScalars *st, History h, int iter, RedScratch red,
+                                 cudaStream_t s);
+cudaError_t launch_dslash32_cg(const DslashCall &c, Field r, Field t_save, CGScalars *st, History h, int iter,
+                               RedScratch red, cudaStream_t s);
+// chooses (once per volume, k and format) how many RHS each stencil thread handles
+cudaError_t autotune_dslash32(const DslashCall &c, cudaStream_t s);
+
+// dslash_dd.cu: double-float (FP32-pair) stencil for residual replacements.  dd fields
+// have the FP64 layout with float4 (re_hi, im_hi, re_lo, im_lo) per complex number.
+cudaError_t launch_to_dd(const void *fp64, void *dd, long n_complex, cudaStream_t s);
+cudaError_t launch_from_dd(const void *dd, void *fp64, long n_complex, cudaStream_t s);
+cudaError_t launch_dslash_dd(const DslashCall &c, const void *gauge_dd, const void *in_dd, void *out_dd,
+                             cudaStream_t s);
+cudaError_t launch_dslash_dd_resid(const DslashCall &c, const void *gauge_dd, const void *in_dd, Field b, Field r,
+                                   CGScalars *st, History h, int iter, bool set_rho, RedScratch red, cudaStream_t s);
 
 // ---------------------------- blas.cu -------------------------------------------------
 // natural FP64 [k][V][12] complex  <->  internal field
@@ -90,8 +110,11 @@ cudaError_t launch_combine(Field out, double ca, Field a, double cb, Field b, cu
 // per-RHS ||f||^2 -> st[r].aux;  with as_rho: also rho = aux, rho_prev = aux, history rho[iter]
 // and target = tol2 * bnorm2[r] computed elsewhere (untouched here).
 cudaError_t launch_norm2(Field f, CGScalars *st, bool as_rho, History h, int iter, RedScratch red, cudaStream_t s);
-// CG step 9 + eigCG step 11.13: p = r + beta p (first: p = r); optionally v = r / sqrt(rho)
-cudaError_t launch_pupdate(Field r, Field p, bool first, CGScalars *st, Field v_append, cudaStream_t s);
+// CG step 13 of the previous iteration (x += alpha p, if pending), step 9 (p = r + beta p;
+// first: p = r) and eigCG step 11.13 (v = r / sqrt(rho), optional)
+cudaError_t launch_pupdate(Field r, Field p, Field x, bool first, CGScalars *st, Field v_append, cudaStream_t s);
+// applies a pending x += alpha p for every RHS and clears the pending flags
+cudaError_t launch_xflush(Field p, Field x, CGScalars *st, int k, cudaStream_t s);
 // set up per-RHS scalars: target = tol^2 * aux (aux must hold ||b||^2), active = 1, breakdown = 0
 cudaError_t launch_cg_init(CGScalars *st, int k, double tol, History h, cudaStream_t s);
 

@@ -1,0 +1,220 @@
+"""Continuous-batching solve service over many operators (gauge field, quark mass).
+
+Each operator keeps its own deflation basis resident on the device, so earlier
+requests deflate later ones (the incremental idea of Sec. 4): while the basis is
+still growing a request is solved with eigCG(nev, m) and its Ritz vectors are
+added (Sec. 4 box); once the basis is full, every request that is waiting for
+that operator is taken into one batched init-CG call (Eq. 1, restarted as in
+Sec. 5.3) of up to max_rhs right-hand sides.
+
+Every operator has its own worker thread and CUDA stream, so solves for
+different operators overlap on the GPU; requests that arrive while a batch is
+running are admitted into the next batch of their operator.  Operators are
+admitted under an HBM budget: an operator is activated (its device memory
+allocated) only when its footprint fits next to the active ones; otherwise its
+requests wait until an idle operator has been retired.
+
+This module only schedules calls; all arithmetic runs in libeigcg.so.
+"""
+from __future__ import annotations
+
+import queue
+import threading
+import time
+from concurrent.futures import Future
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import _lib
+from .api import Basis, Op
+
+
+@dataclass
+class OpSpec:
+    key: str
+    dims: tuple
+    m_q: float
+    gauge: np.ndarray
+    prec: int = 32
+    max_rhs: int = 16
+    nev: int = 10
+    m: int = 100
+    basis_max: int = 240
+    tol: float = 1e-8
+    restart_tol: float = 1e-6
+
+    def footprint(self) -> int:
+        """Device bytes of an active operator: links, workspace, window, basis."""
+        V = int(np.prod(self.dims))
+        sp = {64: 192, 32: 96, 16: 52}[self.prec]
+        wide = 192 if self.prec == 64 else 96
+        links = V * 4 * (144 + {64: 0, 32: 48, 16: 24}[self.prec])
+        work = V * self.max_rhs * (3 * sp + 5 * 192 + 2 * wide + 2 * 192) + V * 96 * 4
+        window = V * wide * (self.m + 3)
+        basis = V * wide * (self.basis_max + self.nev + 16 + 16)
+        return links + work + window + basis
+
+
+@dataclass
+class Request:
+    key: str
+    b: np.ndarray
+    submitted: float = 0.0
+    future: Future = field(default_factory=Future)
+
+
+class _Worker:
+    def __init__(self, server: "Server", spec: OpSpec):
+        self.server = server
+        self.spec = spec
+        self.q: "queue.Queue[Request]" = queue.Queue()
+        self.op = None
+        self.basis = None
+        self.stream = None
+        self.active = False
+        self.busy = False
+        self.last_used = time.perf_counter()
+        self.thread = threading.Thread(target=self._run, daemon=True, name=f"eig-{spec.key}")
+        self.thread.start()
+
+    def activate(self):
+        import torch
+
+        self.stream = torch.cuda.Stream()
+        s = self.spec
+        self.op = Op(s.gauge, s.dims, s.m_q, prec=s.prec, max_rhs=s.max_rhs)
+        self.basis = Basis(self.op, s.basis_max + s.nev)
+        self.active = True
+
+    def retire(self):
+        if self.basis is not None:
+            self.basis.close()
+        if self.op is not None:
+            self.op.close()
+        self.op = self.basis = None
+        self.active = False
+
+    def _take(self, first: Request, limit: int):
+        batch = [first]
+        while len(batch) < limit:
+            try:
+                batch.append(self.q.get_nowait())
+            except queue.Empty:
+                break
+        return batch
+
+    def _run(self):
+        while True:
+            req = self.q.get()
+            if req is None:
+                return
+            self.server._admit(self)
+            self.busy = True
+            try:
+                self._serve(req)
+            finally:
+                self.busy = False
+                self.last_used = time.perf_counter()
+                self.server._released()
+
+    def _serve(self, req: Request):
+        import torch
+
+        s = self.spec
+        growing = self.basis.size + s.nev <= s.basis_max
+        with torch.cuda.stream(self.stream):
+            if growing:
+                b = torch.from_numpy(req.b).to("cuda", non_blocking=False)
+                x = torch.zeros_like(b)
+                st = self.op.eigcg_solve(b, x, s.nev, s.m, s.tol, basis=self.basis, stream=self.stream)
+                self.basis.grow(stream=self.stream)
+                self._finish([req], x.reshape(1, -1), [st], "eigcg")
+                return
+            batch = self._take(req, s.max_rhs)
+            k = 1
+            while k < len(batch):
+                k *= 2
+            B = np.zeros((k, req.b.size), dtype=np.complex128)
+            for i, r in enumerate(batch):
+                B[i] = r.b
+            Bd = torch.from_numpy(B).to("cuda")
+            Xd = torch.zeros_like(Bd)
+            sts = self.op.initcg_solve(Bd, Xd, s.tol, s.restart_tol, basis=self.basis, k=k, stream=self.stream)
+            self._finish(batch, Xd, sts[: len(batch)], "initcg")
+
+    def _finish(self, batch, X, sts, kind):
+        X = X.cpu().numpy()
+        now = time.perf_counter()
+        for i, r in enumerate(batch):
+            res = {"x": X[i].copy(), "stats": sts[i], "kind": kind, "latency_ms": (now - r.submitted) * 1e3,
+                   "basis_size": self.basis.size, "batch": len(batch)}
+            self.server._record(r.key, res)
+            r.future.set_result(res)
+
+
+class Server:
+    """submit(key, b) -> Future[dict(x, stats, kind, latency_ms, basis_size, batch)]."""
+
+    def __init__(self, specs, hbm_budget_bytes: float = 150e9):
+        self.budget = float(hbm_budget_bytes)
+        self.specs = {s.key: s for s in specs}
+        for s in specs:
+            if s.footprint() > self.budget:
+                raise ValueError(f"operator {s.key} alone needs {s.footprint() / 1e9:.1f} GB > budget")
+        self.cv = threading.Condition()
+        self.used = 0.0
+        self.workers = {s.key: _Worker(self, s) for s in specs}
+        self.latencies = []
+        self.records = []
+        self.max_used = 0.0
+
+    def submit(self, key: str, b: np.ndarray) -> Future:
+        req = Request(key, np.ascontiguousarray(b, dtype=np.complex128).reshape(-1))
+        req.submitted = time.perf_counter()
+        self.workers[key].q.put(req)
+        return req.future
+
+    # admission by HBM budget: activate the operator, retiring idle ones if needed
+    def _admit(self, w: _Worker):
+        need = w.spec.footprint()
+        with self.cv:
+            while not w.active:
+                if self.used + need <= self.budget:
+                    self.used += need
+                    self.max_used = max(self.max_used, self.used)
+                    w.activate()
+                    break
+                idle = [o for o in self.workers.values() if o.active and not o.busy and o.q.empty() and o is not w]
+                if idle:
+                    victim = min(idle, key=lambda o: o.last_used)
+                    victim.retire()
+                    self.used -= victim.spec.footprint()
+                    continue
+                self.cv.wait(timeout=0.05)
+
+    def _released(self):
+        with self.cv:
+            self.cv.notify_all()
+
+    def _record(self, key, res):
+        with self.cv:
+            self.latencies.append(res["latency_ms"])
+            self.records.append((key, res["kind"], res["stats"]["iters"], res["latency_ms"], res["batch"]))
+
+    def percentiles(self):
+        a = np.array(self.latencies)
+        return {"p50_ms": float(np.percentile(a, 50)), "p99_ms": float(np.percentile(a, 99)), "n": int(a.size)}
+
+    def close(self):
+        for w in self.workers.values():
+            w.q.put(None)
+        for w in self.workers.values():
+            w.thread.join(timeout=60)
+            w.retire()
+
+
+def poisson_arrivals(rate_per_s: float, n: int, seed: int) -> np.ndarray:
+    """n arrival times (seconds from 0) of a Poisson process of the given rate."""
+    rng = np.random.default_rng(seed)
+    return np.cumsum(rng.exponential(1.0 / rate_per_s, size=n))
