@@ -159,6 +159,24 @@ eig_status eig_profile_enable(int on);
 eig_status eig_profile_reset(void);
 eig_status eig_profile_read(eig_kernel_stat *out, int max, int *n);
 
+/* Allocation-free M, M^H or A = M^H M (which 0, 1, 2) on one FP64 RHS.  The paper
+ * has no counterpart: this entry point exists for callers that may not allocate
+ * device memory during the call (work inside a stream capture, memory owned by
+ * another allocator, a device already reserved in full), which eig_op_apply cannot
+ * serve because an op handle allocates its own buffers.
+ * gauge ([V][4][3][3] complex), in and out ([V][4][3] complex): DEVICE pointers in
+ * the natural layout above, owned by the caller; in and out must not overlap.
+ * dims: each >= 2, Lx*Ly*Lz*Lt <= 65536 sites (EIG_ERR_BUDGET beyond).
+ * A keeps its intermediate M in in a static device array of 65536 sites (12.6 MB)
+ * shared by every call: it holds the last call's data (nothing in it needs to start
+ * at zero), and calls that overlap on the GPU race on it.  The first call on each
+ * device (with that device current) looks up the array's address and caches it;
+ * make that call before any stream capture.  Asynchronous on `stream`.
+ * Errors: EIG_ERR_ARG (null or host pointers, bad which/dims), EIG_ERR_BUDGET,
+ * EIG_ERR_CUDA. */
+eig_status eig_wilson_apply_noalloc(const double *gauge, const int dims[4], double m_q, int which, const double *in,
+                                    double *out, void *stream);
+
 /* Message of the calling thread's last error ("" if none). */
 const char *eig_last_error(void);
 

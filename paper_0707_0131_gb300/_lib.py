@@ -75,6 +75,7 @@ SIGNATURES = {
     "eig_profile_enable": [_I],
     "eig_profile_reset": [],
     "eig_profile_read": [_P, _I, _P],
+    "eig_wilson_apply_noalloc": [_P, _P, _D, _I, _P, _P, _P],
     "eig_last_error": [],
 }
 
@@ -242,6 +243,15 @@ def eig_profile_read() -> dict:
     arr = (KernelStat * max(n.value, 1))()
     _check(load().eig_profile_read(arr, n.value, ctypes.byref(n)))
     return {a.name.decode(): {"launches": a.launches, "ms": a.ms, "bytes": a.bytes} for a in arr[: n.value]}
+
+
+def eig_wilson_apply_noalloc(gauge, dims, m_q: float, which: int, vin, vout, stream=None) -> None:
+    """M, M^H or A on one RHS without any device allocation.  gauge, vin and vout
+    are complex128 CUDA tensors in the natural layout (gauge [V][4][3][3], vectors
+    [V][4][3]); vin and vout must not overlap.  Asynchronous on `stream`."""
+    d = (ctypes.c_int * 4)(*[int(v) for v in dims])
+    _check(load().eig_wilson_apply_noalloc(_ptr(gauge), d, float(m_q), int(which), _ptr(vin), _ptr(vout),
+                                           _stream(stream)))
 
 
 def eig_last_error() -> str:

@@ -240,6 +240,9 @@ namespace eig {
 
 static void set_error(const Error &e) { g_last_error = e.msg; }
 
+// lets entry points defined in other files report a message through eig_last_error
+void set_last_error_message(const char *msg) { g_last_error = msg ? msg : ""; }
+
 static bool is_device_ptr(const void *p) {
     cudaPointerAttributes a;
     cudaError_t e = cudaPointerGetAttributes(&a, p);
