@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--serve-basis", type=int, default=40)
     ap.add_argument("--budget-gb", type=float, default=150.0)
     ap.add_argument("--prec", type=int, default=32)
+    ap.add_argument("--links", type=int, default=12, choices=[12, 18],
+                    help="FP32 link storage: 12 reals (third row rebuilt) or all 18")
     ap.add_argument("--which", type=int, default=2, help="dslash mode: 0 M, 1 M^H, 2 A")
     ap.add_argument("--reps", type=int, default=20)
     return ap.parse_args()
@@ -194,7 +196,7 @@ def run_dslash(a):
     dims = fx.LATTICES[a.lattice]
     m_q, _ = mass_for(a.lattice, a.kappa)
     gauge = fx.make_gauge(dims, fx.GAUGE_SEEDS[a.lattice])
-    op = Op(gauge, dims, m_q, prec=a.prec, max_rhs=a.k)
+    op = Op(gauge, dims, m_q, prec=a.prec, max_rhs=a.k, compress12=a.links == 12)
     x = torch.from_numpy(fx.make_rhs(dims, 7, a.k)).cuda()
     y = torch.empty_like(x)
     for _ in range(3):
@@ -207,7 +209,8 @@ def run_dslash(a):
     prof = _lib.eig_profile_read()
     peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"] \
         if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
-    out = {"mode": "dslash", "lattice": a.lattice, "k": a.k, "prec": a.prec, "which": a.which, "kernels": {}}
+    out = {"mode": "dslash", "lattice": a.lattice, "k": a.k, "prec": a.prec, "links": a.links, "which": a.which,
+           "kernels": {}}
     for n, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"]):
         gbs = v["bytes"] / (v["ms"] / 1e3) / 1e9 if v["ms"] > 0 else None
         out["kernels"][n] = {"launches": v["launches"], "ms_per_launch": v["ms"] / max(1, v["launches"]),
@@ -332,7 +335,7 @@ def main():
     m_q, mass_src = mass_for(a.lattice, a.kappa)
     gauge = fx.make_gauge(dims, fx.GAUGE_SEEDS[a.lattice])
     k = a.k
-    op = Op(gauge, dims, m_q, prec=32, max_rhs=k)
+    op = Op(gauge, dims, m_q, prec=32, max_rhs=k, compress12=a.links == 12)
     basis = Basis(op, a.basis + a.nev)
     nrhs_id = [0]
 
@@ -474,8 +477,8 @@ def main():
                "config": {"workload": f"{a.lattice} Wilson, m_q={m_q} ({mass_src}, cond(A)~{a.kappa}), "
                                       f"per step 1 eigCG({a.nev},{a.m}) + grow + k={k} batched init-CG, "
                                       f"basis {l0} FP32 vectors, tol {a.tol}, restart {a.restart_tol}",
-                          "lattice": a.lattice, "k": k, "basis": l0, "storage": "fp32 spinors, 12-real fp32 links, "
-                          "fp64 reliable updates", "l2": "inputs larger than L2 (each field >= 85 MB)",
+                          "lattice": a.lattice, "k": k, "basis": l0, "storage": f"fp32 spinors, {a.links}-real fp32 links, "
+                          "double-float residual replacements, fp64 final residual", "l2": "inputs larger than L2 (each field >= 85 MB)",
                           "parallelism": f"replicas{world}"},
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                "clocks": clk, "plain_fp64_eigcg": plain,

@@ -40,6 +40,7 @@ struct KArgs {
     CGScalars *st;
     double *h_alpha, *h_beta, *h_rho;
     int iter;
+    const int *jbase;  // device iteration base added to iter (null: none)
     double *partials;
     unsigned *counter;
 };
@@ -260,7 +261,7 @@ __global__ void __launch_bounds__(128) k_dslash(const KArgs a) {
     const int k = a.k;
     CGScalars *const sts = a.st;
     double *const h_alpha = a.h_alpha, *const h_beta = a.h_beta, *const h_rho = a.h_rho;
-    const int iter = a.iter, set_rho = a.set_rho;
+    const int iter = a.iter + (a.jbase ? *a.jbase : 0), set_rho = a.set_rho;
     grid_reduce_rhs(bs, k, a.partials, a.counter, smem, [=](int r, double tot) {
         CGScalars &st = sts[r];
         const long hi = (long)iter * k + r;
@@ -443,6 +444,7 @@ cudaError_t launch_dslash_norm(const DslashCall &c, CGScalars *st, History h, in
     a.h_beta = h.beta;
     a.h_rho = h.rho;
     a.iter = iter;
+    a.jbase = h.jbase;
     a.partials = red.partials;
     a.counter = red.counter;
     if (c.in.prec != P64) {
@@ -463,6 +465,7 @@ cudaError_t launch_dslash_cg(const DslashCall &c, Field r, Field t_save, CGScala
     a.h_beta = h.beta;
     a.h_rho = h.rho;
     a.iter = iter;
+    a.jbase = h.jbase;
     a.partials = red.partials;
     a.counter = red.counter;
     if (c.in.prec != P64) {
@@ -482,6 +485,7 @@ cudaError_t launch_dslash_resid(const DslashCall &c, Field b, Field r, CGScalars
     a.h_beta = h.beta;
     a.h_rho = h.rho;
     a.iter = iter;
+    a.jbase = h.jbase;
     a.set_rho = set_rho;
     a.partials = red.partials;
     a.counter = red.counter;

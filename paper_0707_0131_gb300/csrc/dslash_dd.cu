@@ -280,6 +280,30 @@ __global__ void k_from_dd(const float4 *__restrict__ in, double2 *__restrict__ o
     }
 }
 
+// kc FP32 fields of k = 1 (one per column, column c at cols + c * cstride float4s)
+// -> double-float RHS-inner field of kc RHS (low parts zero)
+__global__ void k_cols32_to_dd(const float4 *__restrict__ cols, long cstride, unsigned V, unsigned kc,
+                               float4 *__restrict__ dd) {
+    const unsigned n = V * 12u * kc;
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const unsigned q = i % kc, rest = i / kc, s = rest % V, e = rest / V;
+        const float4 f = cols[(long)q * cstride + (long)(e >> 1) * V + s];
+        dd[i] = (e & 1) ? make_float4(f.z, f.w, 0.f, 0.f) : make_float4(f.x, f.y, 0.f, 0.f);
+    }
+}
+
+// double-float RHS-inner field of kc RHS -> kc FP32 fields of k = 1, rounded
+__global__ void k_dd_to_cols32(const float4 *__restrict__ dd, unsigned V, unsigned kc, float4 *__restrict__ cols,
+                               long cstride) {
+    const unsigned n = V * 6u * kc;
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const unsigned q = i % kc, rest = i / kc, s = rest % V, c = rest / V;
+        const float4 a = dd[((2 * c) * V + s) * kc + q], b = dd[((2 * c + 1) * V + s) * kc + q];
+        cols[(long)q * cstride + (long)c * V + s] =
+            make_float4(__fadd_rn(a.x, a.z), __fadd_rn(a.y, a.w), __fadd_rn(b.x, b.z), __fadd_rn(b.y, b.w));
+    }
+}
+
 int grid_for(unsigned work) {
     long g = ((long)work + 127) / 128;
     const long cap = (long)device_sm_count() * 8;
@@ -300,6 +324,22 @@ cudaError_t launch_from_dd(const void *dd, void *fp64, long n, cudaStream_t s) {
     ProfScope prof("from_dd", (double)n * 32.0, s);
     k_from_dd<<<grid_for((unsigned)n), 128, 0, s>>>(static_cast<const float4 *>(dd), static_cast<double2 *>(fp64),
                                                       (unsigned)n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cols32_to_dd(const void *cols, long cstride_f4, long V, int kc, void *dd, cudaStream_t s) {
+    const unsigned n = (unsigned)(V * 12 * kc);
+    ProfScope prof("cols_to_dd", (double)n * 24.0, s);
+    k_cols32_to_dd<<<grid_for(n), 128, 0, s>>>(static_cast<const float4 *>(cols), cstride_f4, (unsigned)V,
+                                                (unsigned)kc, static_cast<float4 *>(dd));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dd_to_cols32(const void *dd, long V, int kc, void *cols, long cstride_f4, cudaStream_t s) {
+    const unsigned n = (unsigned)(V * 6 * kc);
+    ProfScope prof("dd_to_cols", (double)n * 48.0, s);
+    k_dd_to_cols32<<<grid_for(n), 128, 0, s>>>(static_cast<const float4 *>(dd), (unsigned)V, (unsigned)kc,
+                                                static_cast<float4 *>(cols), cstride_f4);
     return cudaGetLastError();
 }
 

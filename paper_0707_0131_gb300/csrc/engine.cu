@@ -172,6 +172,21 @@ struct eig_op_s {
     DevBuf win, tprev, tcur, col_off, qz, wv;
     int win_slots = 0;
     std::mutex mu;
+    // CUDA graphs of CHECK plain CG iterations (init-CG), one per buffer set
+    struct CgGraph {
+        cudaGraphExec_t exec = nullptr;
+        std::vector<const void *> key;
+        ProfRecord rec;
+    };
+    std::vector<CgGraph> graphs;
+    DevBuf jbase_dev;  // iteration base the replayed kernels add to their offsets
+    PinBuf jbase_h;
+    cudaStream_t cap_stream = nullptr;  // private stream the graphs are captured on
+    ~eig_op_s() {
+        for (auto &g : graphs)
+            if (g.exec) cudaGraphExecDestroy(g.exec);
+        if (cap_stream) cudaStreamDestroy(cap_stream);
+    }
 
     long ncomplex() const { return V * 12; }
     size_t wfield_bytes() const { return field_bytes(wprec, V, 1); }
@@ -231,6 +246,7 @@ struct eig_basis_s {
     std::vector<cd> H, Lc;  // H = U^H A U and its Cholesky factor (row-major l x l)
     bool chol_ok = true;
     DevBuf C, Y;            // device small matrices
+    DevBuf tcpart, tcerr;   // partial sums and error flag of the tensor-core U^H R
     PinBuf Ch;
     std::mutex mu;
     long fsize() const { return op->V * 12; }  // complex entries per field
@@ -453,6 +469,67 @@ static void check_breakdown(const Solve &sv) {
         if (sv.sth[q].breakdown) throw Error{EIG_ERR_BREAKDOWN, "CG breakdown (p^H A p <= 0, NaN or Inf)"};
 }
 
+// Plain CG iterations of init-CG run as replays of a captured graph of CHECK
+// iterations unless kernel timing is on (its events would be captured too) or
+// EIG_CG_GRAPH=0 is set.
+static bool cg_graphs_enabled() {
+    if (prof_timing()) return false;
+    const char *e = getenv("EIG_CG_GRAPH");
+    return !(e && e[0] == '0');
+}
+
+// The graph of CHECK iterations j0 + 1 .. j0 + CHECK for this solve's buffers (j0 is
+// read by the kernels from op->jbase_dev), captured on first use.
+static cudaGraphExec_t cg_graph(Solve &sv, eig_op_s *op) {
+    const std::vector<const void *> key = {(const void *)(long)sv.k, sv.r.v.data, sv.p.v.data, sv.u.v.data,
+                                           sv.xlo.v.data, sv.st, sv.h.alpha, sv.h.beta, sv.h.rho,
+                                           (const void *)(long)op->prec};
+    for (auto &g : op->graphs)
+        if (g.key == key) return g.exec;
+    op->jbase_dev.ensure(16);
+    op->jbase_h.ensure(16);
+    History hg = sv.h;
+    hg.jbase = op->jbase_dev.as<int>();
+    eig_op_s::CgGraph gr;
+    gr.key = key;
+    if (!op->cap_stream) CUDA_CK(cudaStreamCreateWithFlags(&op->cap_stream, cudaStreamNonBlocking));
+    // captured on a private stream (the caller's may be the legacy stream, which
+    // cannot be captured); the graph is launched on the caller's stream
+    cudaStream_t s = op->cap_stream;
+    cudaGraph_t graph = nullptr;
+    CUDA_CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    prof_record_begin(&gr.rec);
+    cudaError_t e = cudaSuccess;
+    for (int t = 1; t <= CHECK && e == cudaSuccess; t++) {
+        e = launch_pupdate(sv.r, sv.p, sv.xlo, false, sv.st, null_field(), s);
+        if (e == cudaSuccess)
+            e = launch_dslash_norm(op->call(sv.p, sv.u, false, op->prec == P64), sv.st, hg, t, sv.red, s);
+        if (e == cudaSuccess)
+            e = launch_dslash_cg(op->call(sv.u, sv.u, true, op->prec == P64), sv.r, null_field(), sv.st, hg, t,
+                                 sv.red, s);
+    }
+    prof_record_end();
+    const cudaError_t e2 = cudaStreamEndCapture(s, &graph);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        throw Error{EIG_ERR_CUDA, std::string("CG graph capture failed: ") +
+                                      cudaGetErrorString(e != cudaSuccess ? e : e2)};
+    }
+    const cudaError_t e3 = cudaGraphInstantiate(&gr.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e3 != cudaSuccess) {
+        cudaGetLastError();
+        throw Error{EIG_ERR_CUDA, std::string("CG graph instantiation failed: ") + cudaGetErrorString(e3)};
+    }
+    if (op->graphs.size() >= 4) {
+        cudaGraphExecDestroy(op->graphs.front().exec);
+        op->graphs.erase(op->graphs.begin());
+    }
+    op->graphs.push_back(std::move(gr));
+    return op->graphs.back().exec;
+}
+
 // Runs CG iterations until every RHS is inactive or max_iter.  With a window,
 // performs the eigCG additions.  Returns false if max_iter was hit.
 static bool cg_run(Solve &sv, int max_iter, Window *w, eig_op_s *op) {
@@ -484,6 +561,18 @@ static bool cg_run(Solve &sv, int max_iter, Window *w, eig_op_s *op) {
             }
             sv.j_checked = sv.j;
             since = 0;
+        }
+        if (!w && since == 0 && sv.j >= 1 && sv.j + CHECK <= max_iter && cg_graphs_enabled()) {
+            // CHECK plain iterations as one replayed CUDA graph
+            cudaGraphExec_t g = cg_graph(sv, op);
+            *op->jbase_h.as<int>() = sv.j;
+            CUDA_CK(cudaMemcpyAsync(op->jbase_dev.p, op->jbase_h.p, sizeof(int), cudaMemcpyHostToDevice, s));
+            CUDA_CK(cudaGraphLaunch(g, s));
+            for (const auto &gr : op->graphs)
+                if (gr.exec == g) prof_replay(gr.rec);
+            sv.j += CHECK;
+            since = CHECK;
+            continue;
         }
         const int j = ++sv.j;
         since++;
@@ -598,7 +687,7 @@ static bool cg_finish(Solve &sv, int max_iter, Window *w, eig_op_s *op, int &ext
 
 // Picks the stencil variant for this k on the op's own buffers (once per op shape).
 static void tune_for(eig_op_s *op, int k, cudaStream_t s) {
-    if (op->prec == P64 || k < 2) return;
+    if (op->prec == P64) return;
     CUDA_CK(autotune_dslash32(op->call(op->p.view(k), op->u.view(k), false, false), s));
 }
 
@@ -693,6 +782,38 @@ static void refactor(eig_basis_s *B) {
     B->chol_ok = l == 0 || dense::cholesky(l, B->Lc.data());
 }
 
+// U^H r of the deflation on the tensor cores (FP32 windows): EIG_GEMM_TC=1 in the
+// environment selects it, read at every call.
+static bool tc_gemm_enabled() {
+    const char *e = getenv("EIG_GEMM_TC");
+    return e && e[0] == '1';
+}
+
+// C = A^H B into B->C (device) and B->Ch (host; the stream is synchronised).  FP32
+// column sets go to the tensor cores when tc_gemm_enabled(); their kernel's error
+// flag is read back with C and checked here.
+static const cd *ahb_to_host(eig_basis_s *B, const ColSet &A, const ColSet &Bc, long nrow, cudaStream_t s) {
+    eig_op_s *op = B->op;
+    const size_t cb = (size_t)A.ncols * Bc.ncols * 16;
+    B->C.ensure(cb);
+    B->Ch.ensure(cb + 16);
+    const bool tc = tc_gemm_enabled() && tc_ahb_ok(A, Bc);
+    if (tc) {
+        B->tcpart.ensure(tc_ahb_partials_bytes(nrow, A.ncols, Bc.ncols));
+        B->tcerr.ensure(16);
+        CUDA_CK(cudaMemsetAsync(B->tcerr.p, 0, 16, s));
+        CUDA_CK(launch_tc_ahb(A, Bc, nrow, B->C.as<double>(), B->tcpart.as<double>(), B->tcerr.as<int>(), s));
+        CUDA_CK(cudaMemcpyAsync((char *)B->Ch.p + cb, B->tcerr.p, 4, cudaMemcpyDeviceToHost, s));
+    } else {
+        CUDA_CK(launch_gemm_ahb(A, Bc, nrow, B->C.as<double>(), op->red(), s));
+    }
+    CUDA_CK(cudaMemcpyAsync(B->Ch.p, B->C.p, cb, cudaMemcpyDeviceToHost, s));
+    sync(s);
+    if (tc && *reinterpret_cast<const int *>((const char *)B->Ch.p + cb) != 0)
+        throw Error{EIG_ERR_TIMEOUT, "tensor-core A^H B: a bounded wait in the kernel gave up"};
+    return B->Ch.as<cd>();
+}
+
 // x64 <- x64 + U H^{-1} U^H r64 for k RHS (r64 given in FP64).
 static void deflate_into(eig_basis_s *B, Field r64, Field x64, cudaStream_t s) {
     eig_op_s *op = B->op;
@@ -703,14 +824,9 @@ static void deflate_into(eig_basis_s *B, Field r64, Field x64, cudaStream_t s) {
     CUDA_CK(launch_combine(rsv, 1.0, r64, 0.0, null_field(), s));
     const bool f64 = op->wprec == P64;
     ColSet R = field_cols(rsv.v.data, f64, k, B->fsize(), k, true);
-    B->C.ensure((size_t)l * k * 16);
-    CUDA_CK(launch_gemm_ahb(basis_cols(B, 0, l), R, op->ncomplex(), B->C.as<double>(), op->red(), s));
-    B->Ch.ensure((size_t)l * k * 16);
-    CUDA_CK(cudaMemcpyAsync(B->Ch.p, B->C.p, (size_t)l * k * 16, cudaMemcpyDeviceToHost, s));
-    sync(s);
+    const cd *Cc = ahb_to_host(B, basis_cols(B, 0, l), R, op->ncomplex(), s);
     // solve H y = c per RHS (C is l x k row-major)
     std::vector<cd> Yc((size_t)l * k);
-    const cd *Cc = B->Ch.as<cd>();
     for (int a = 0; a < l; a++)
         for (int q = 0; q < k; q++) Yc[(size_t)q * l + a] = Cc[(size_t)a * k + q];
     dense::chol_solve(l, B->Lc.data(), Yc.data(), k);
@@ -1063,14 +1179,9 @@ eig_status eig_basis_grow(eig_basis B, void *stream) {
     ColSet P = field_cols(B->pend.p, f64, 1, B->fsize(), np, false);
     // classical Gram-Schmidt against U, twice
     if (l > 0) {
-        B->C.ensure((size_t)l * np * 16);
-        B->Ch.ensure((size_t)l * np * 16);
         for (int pass = 0; pass < 2; pass++) {
-            CUDA_CK(launch_gemm_ahb(basis_cols(B, 0, l), P, nrow, B->C.as<double>(), op->red(), s));
-            CUDA_CK(cudaMemcpyAsync(B->Ch.p, B->C.p, (size_t)l * np * 16, cudaMemcpyDeviceToHost, s));
-            sync(s);
+            const double *c = reinterpret_cast<const double *>(ahb_to_host(B, basis_cols(B, 0, l), P, nrow, s));
             std::vector<double> negc((size_t)l * np * 2);
-            const double *c = B->Ch.as<double>();
             for (size_t q = 0; q < negc.size(); q++) negc[q] = -c[q];
             B->Y.ensure(negc.size() * sizeof(double));
             CUDA_CK(cudaMemcpyAsync(B->Y.p, negc.data(), negc.size() * sizeof(double), cudaMemcpyHostToDevice, s));
@@ -1079,12 +1190,8 @@ eig_status eig_basis_grow(eig_basis B, void *stream) {
         }
     }
     // orthonormalise the remainders among themselves: pivoted Cholesky of the Gram matrix
-    B->C.ensure((size_t)np * np * 16);
-    B->Ch.ensure((size_t)np * np * 16);
-    CUDA_CK(launch_gemm_ahb(P, P, nrow, B->C.as<double>(), op->red(), s));
-    CUDA_CK(cudaMemcpyAsync(B->Ch.p, B->C.p, (size_t)np * np * 16, cudaMemcpyDeviceToHost, s));
-    sync(s);
-    std::vector<cd> G(B->Ch.as<cd>(), B->Ch.as<cd>() + (size_t)np * np);
+    const cd *Gp = ahb_to_host(B, P, P, nrow, s);
+    std::vector<cd> G(Gp, Gp + (size_t)np * np);
     const double drop = f64 ? 1e-10 : 1e-4;
     std::vector<cd> Rinv;
     std::vector<int> keep;
@@ -1108,10 +1215,8 @@ eig_status eig_basis_grow(eig_basis B, void *stream) {
     {
         // second pass: the remainders can be nearly dependent, so orthonormalise again
         ColSet Un = basis_cols(B, l, r);
-        CUDA_CK(launch_gemm_ahb(Un, Un, nrow, B->C.as<double>(), op->red(), s));
-        CUDA_CK(cudaMemcpyAsync(B->Ch.p, B->C.p, (size_t)r * r * 16, cudaMemcpyDeviceToHost, s));
-        sync(s);
-        std::vector<cd> G2(B->Ch.as<cd>(), B->Ch.as<cd>() + (size_t)r * r);
+        const cd *G2p = ahb_to_host(B, Un, Un, nrow, s);
+        std::vector<cd> G2(G2p, G2p + (size_t)r * r);
         std::vector<cd> R2;
         std::vector<int> keep2;
         gram_orth(G2, r, 0.0, R2, keep2);
@@ -1129,23 +1234,34 @@ eig_status eig_basis_grow(eig_basis B, void *stream) {
                                 (size_t)r * op->wfield_bytes(), cudaMemcpyDeviceToDevice, s));
         sync(s);
     }
-    // W = A V-bar with the FP64 operator, stored in window precision
-    Field x64 = op->x64.view(1), r64f = op->b64.view(1);
-    for (int c = 0; c < r; c++) {
-        Field uc = field_at(op->wprec, (char *)B->U.p + (size_t)(l + c) * op->wfield_bytes(), op->V, 1);
-        Field wc = field_at(op->wprec, (char *)B->W.p + (size_t)c * op->wfield_bytes(), op->V, 1);
-        CUDA_CK(launch_combine(x64, 1.0, uc, 0.0, null_field(), s));
-        apply_A64(op, x64, r64f, s);
-        CUDA_CK(launch_combine(wc, 1.0, r64f, 0.0, null_field(), s));
+    if (op->prec != P64) {
+        // W = A V-bar in double-float arithmetic (about 44 bits, far below the FP32
+        // rounding of the stored W), up to max_rhs columns per stencil launch
+        const long cstride = (long)(op->wfield_bytes() / 16);
+        for (int c0 = 0; c0 < r; c0 += op->max_rhs) {
+            const int n = std::min(op->max_rhs, r - c0);
+            Field xin = op->r64.view(n), mid = op->u64.view(n), wout = op->x64.view(n);
+            CUDA_CK(launch_cols32_to_dd((char *)B->U.p + (size_t)(l + c0) * op->wfield_bytes(), cstride, op->V, n,
+                                        xin.v.data, s));
+            CUDA_CK(launch_dslash_dd(op->call(xin, mid, false, true), op->gauge_dd.p, xin.v.data, mid.v.data, s));
+            CUDA_CK(launch_dslash_dd(op->call(mid, wout, true, true), op->gauge_dd.p, mid.v.data, wout.v.data, s));
+            CUDA_CK(launch_dd_to_cols32(wout.v.data, op->V, n, (char *)B->W.p + (size_t)c0 * op->wfield_bytes(),
+                                        cstride, s));
+        }
+    } else {
+        // W = A V-bar with the FP64 operator
+        Field x64 = op->x64.view(1), r64f = op->b64.view(1);
+        for (int c = 0; c < r; c++) {
+            Field uc = field_at(op->wprec, (char *)B->U.p + (size_t)(l + c) * op->wfield_bytes(), op->V, 1);
+            Field wc = field_at(op->wprec, (char *)B->W.p + (size_t)c * op->wfield_bytes(), op->V, 1);
+            CUDA_CK(launch_combine(x64, 1.0, uc, 0.0, null_field(), s));
+            apply_A64(op, x64, r64f, s);
+            CUDA_CK(launch_combine(wc, 1.0, r64f, 0.0, null_field(), s));
+        }
     }
     ColSet Wc = field_cols(B->W.p, f64, 1, B->fsize(), r, false);
     const int ln = l + r;
-    B->C.ensure((size_t)ln * r * 16);
-    B->Ch.ensure((size_t)ln * r * 16);
-    CUDA_CK(launch_gemm_ahb(basis_cols(B, 0, ln), Wc, nrow, B->C.as<double>(), op->red(), s));
-    CUDA_CK(cudaMemcpyAsync(B->Ch.p, B->C.p, (size_t)ln * r * 16, cudaMemcpyDeviceToHost, s));
-    sync(s);
-    const cd *UW = B->Ch.as<cd>();  // (l + r) x r: rows 0..l-1 = U^H W, rows l.. = V-bar^H W
+    const cd *UW = ahb_to_host(B, basis_cols(B, 0, ln), Wc, nrow, s);  // (l + r) x r: rows 0..l-1 = U^H W, rows l.. = V-bar^H W
     std::vector<cd> Hn((size_t)ln * ln);
     for (int a = 0; a < l; a++)
         for (int bb = 0; bb < l; bb++) Hn[(size_t)a * ln + bb] = B->H[(size_t)a * l + bb];

@@ -46,11 +46,14 @@ struct Field {
 };
 
 // History of CG scalars: alpha[j*k + r] etc. for iterations j = 0..cap-1.
+// With jbase set, the iteration index a kernel is given is relative: the kernel adds
+// *jbase (device), so that one captured block of iterations can be replayed.
 struct History {
     double *alpha;
     double *beta;
     double *rho;
     int cap;
+    const int *jbase = nullptr;
 };
 
 struct DslashCall {
@@ -93,6 +96,10 @@ cudaError_t autotune_dslash32(const DslashCall &c, cudaStream_t s);
 // dslash_dd.cu: double-float (FP32-pair) stencil for residual replacements.  dd fields
 // have the FP64 layout with float4 (re_hi, im_hi, re_lo, im_lo) per complex number.
 cudaError_t launch_to_dd(const void *fp64, void *dd, long n_complex, cudaStream_t s);
+// kc FP32 fields of one RHS each (column c at cols + c * cstride_f4 float4s) <->
+// a double-float RHS-inner field of kc RHS
+cudaError_t launch_cols32_to_dd(const void *cols, long cstride_f4, long V, int kc, void *dd, cudaStream_t s);
+cudaError_t launch_dd_to_cols32(const void *dd, long V, int kc, void *cols, long cstride_f4, cudaStream_t s);
 cudaError_t launch_from_dd(const void *dd, void *fp64, long n_complex, cudaStream_t s);
 cudaError_t launch_dslash_dd(const DslashCall &c, const void *gauge_dd, const void *in_dd, void *out_dd,
                              cudaStream_t s);
@@ -143,6 +150,19 @@ cudaError_t launch_gemm_ay(ColSet A, const double *Y, ColSet Out, double beta_ou
 //   w = t - beta * t_prev  (beta read from *beta_dev).  wv: FP64 complex [nout], device.
 cudaError_t launch_window_restart(ColSet Vw, int m, const double *QZ, int nout, const void *t, const void *t_prev,
                                   const double *beta_dev, long nrows, double *wv, RedScratch red, cudaStream_t s);
+
+// C (nA x nB, FP64 complex, row-major, device) = A^H B on the tensor cores (tcgen05,
+// kind::tf32 with each operand split into TF32 hi + lo parts, three products per K
+// step; FP32 accumulation in TMEM over two K tiles at a time, drained into
+// double-float sums per thread, FP64 sum over CTAs).  A: FP32 fields, one per column (ki = 1, no offsets), column
+// stride a multiple of 2 complex, 16-byte aligned, nA <= 256; B: FP32 column set of
+// nB <= 16 columns, RHS-inner (ki = nB) or one field per column (ki = 1).
+// tc_ahb_ok tells whether a pair qualifies.  *err (device int, zeroed by the caller)
+// becomes non-zero if a bounded wait inside the kernel gave up; C is then invalid.
+bool tc_ahb_ok(const ColSet &A, const ColSet &B);
+size_t tc_ahb_partials_bytes(long nrows, int l, int k);
+cudaError_t launch_tc_ahb(const ColSet &A, const ColSet &B, long nrows, double *C, double *partials, int *err,
+                          cudaStream_t s);
 
 int device_sm_count();
 

@@ -19,6 +19,7 @@ std::mutex g_mu;
 std::vector<Entry> g_entries;
 std::vector<cudaEvent_t> g_pool;
 bool g_timing = false;
+thread_local ProfRecord *g_rec = nullptr;
 
 int slot_of(const char *name) {
     for (size_t i = 0; i < g_entries.size(); i++)
@@ -43,6 +44,10 @@ cudaEvent_t get_event() {
 ProfScope::ProfScope(const char *name, double bytes, cudaStream_t s) : slot(-1), ev(-1), stream(s) {
     std::lock_guard<std::mutex> lk(g_mu);
     slot = slot_of(name);
+    if (g_rec) {
+        g_rec->items.push_back({slot, bytes});
+        return;
+    }
     Entry &e = g_entries[slot];
     e.launches++;
     e.bytes += bytes;
@@ -58,6 +63,23 @@ ProfScope::~ProfScope() {
     if (ev < 0) return;
     std::lock_guard<std::mutex> lk(g_mu);
     cudaEventRecord(g_entries[slot].pending[ev].second, stream);
+}
+
+void prof_record_begin(ProfRecord *rec) { g_rec = rec; }
+void prof_record_end() { g_rec = nullptr; }
+
+void prof_replay(const ProfRecord &rec) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (const auto &it : rec.items) {
+        if (it.first < 0 || it.first >= (int)g_entries.size()) continue;
+        g_entries[it.first].launches++;
+        g_entries[it.first].bytes += it.second;
+    }
+}
+
+bool prof_timing() {
+    std::lock_guard<std::mutex> lk(g_mu);
+    return g_timing;
 }
 
 void prof_enable(bool on) {

@@ -5,6 +5,9 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <utility>
+#include <vector>
+
 namespace eig {
 
 struct ProfScope {
@@ -21,6 +24,18 @@ struct KernelStat {
     double ms;
     double bytes;
 };
+
+// Launches recorded while a stream is captured into a CUDA graph: the capture does
+// not run them, each replay of the graph does.
+struct ProfRecord {
+    std::vector<std::pair<int, double>> items;  // (entry, bytes) per captured launch
+};
+// While active on this thread, ProfScope appends to *rec instead of counting.
+void prof_record_begin(ProfRecord *rec);
+void prof_record_end();
+// Counts one replay of a recorded block.
+void prof_replay(const ProfRecord &rec);
+bool prof_timing();
 
 void prof_enable(bool on);
 void prof_reset();

@@ -1,0 +1,61 @@
+"""Every variant of the FP32-arithmetic stencil against the oracle.
+
+The library picks the fastest of eight variants (staged or direct loads, one or two
+RHS per thread, register budgets, L1 prefetch) per lattice and k; EIG_DSLASH_VARIANT forces one
+for the whole process, so each variant runs in a subprocess of its own.  Each one
+must meet the FP32 (1e-6) and FP16 (5e-3) matvec bars of test_gpu_dslash.py for M,
+M^H and A, on a lattice with a ragged last block and on 8^4, with k = 1 and 4, and
+with the CG epilogue (an init-CG solve reaching 1e-8 in mixed precision).
+"""
+import os
+import subprocess
+import sys
+
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+CHILD = r"""
+import numpy as np, oracle
+from paper_0707_0131_gb300 import api, fixtures as fx
+TOL = {32: 1e-6, 16: 5e-3}
+for dims in [(6, 4, 2, 10), (8, 8, 8, 8)]:
+    gauge = fx.make_gauge(dims, 51)
+    W = oracle.Wilson(dims, -0.1, gauge)
+    for prec in (32, 16):
+        for k in (1, 4):
+            op = api.Op(gauge, dims, -0.1, prec=prec, max_rhs=k)
+            psi = fx.make_rhs(dims, 52, k)
+            for which, f in [(0, W.M), (1, W.Mdag), (2, W.A)]:
+                out = np.empty_like(psi)
+                op.apply(which, psi, out, k)
+                for r in range(k):
+                    ref = f(psi[r])
+                    err = np.linalg.norm(out[r].reshape(-1) - ref) / np.linalg.norm(ref)
+                    assert err < TOL[prec], (dims, prec, k, which, r, err)
+            op.close()
+dims = (8, 8, 8, 8)
+gauge = fx.make_gauge(dims, 53)
+W = oracle.Wilson(dims, 0.05, gauge)
+op = api.Op(gauge, dims, 0.05, prec=32, max_rhs=4)
+B = fx.make_rhs(dims, 54, 4).reshape(4, -1)
+X = np.zeros_like(B)
+st = op.initcg_solve(B, X, tol=1e-8, k=4)
+for r in range(4):
+    assert np.linalg.norm(B[r] - W.A(X[r])) / np.linalg.norm(B[r]) <= 1e-8, (r, st[r])
+op.close()
+print("variant ok")
+"""
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6, 7])
+def test_variant_parity(variant):
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    env = dict(os.environ, EIG_DSLASH_VARIANT=str(variant))
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    p = subprocess.run([sys.executable, "-c", CHILD], env=env, cwd=root, capture_output=True, text=True,
+                       timeout=600)
+    assert p.returncode == 0 and "variant ok" in p.stdout, p.stdout[-2000:] + p.stderr[-4000:]
