@@ -413,13 +413,17 @@ def main():
     else:
         peak, peak_src = 6800.0, "fallback"
     achieved = (kp["bytes"] / kp["launches"]) / (kp["ms"] / kp["launches"] / 1e3) / 1e9
+    # DRAM traffic from an ncu capture of this kernel (configs/traffic_from_ncu.py): the
+    # measured DRAM / algorithmic byte ratio, valid while the stencil sources match
     traffic = None
-    tfile = os.path.join(ROOT, "profiles", "traffic.json")
+    tfile = os.path.join(ROOT, "configs", "traffic.json")
     if os.path.exists(tfile):
-        tj = json.load(open(tfile))
-        src = open(os.path.join(ROOT, "paper_0707_0131_gb300", "csrc", "dslash.cu"), "rb").read()
-        if tj.get(kern, {}).get("dslash_sha1") == hashlib.sha1(src).hexdigest():
-            traffic = tj[kern]["bytes_per_launch"]
+        tj = json.load(open(tfile)).get(kern, {})
+        h = hashlib.sha1()
+        for f in ("dslash32.cuh", "dslash32.cu", "dslash32d_rb1.cu", "dslash32d_rb2.cu"):
+            h.update(open(os.path.join(ROOT, "paper_0707_0131_gb300", "csrc", f), "rb").read())
+        if tj.get("stencil_sha1") == h.hexdigest():
+            traffic = tj["dram_over_algorithmic"] * kp["bytes"] / kp["launches"]
     roofline = {"bound": "hbm", "kernel": kern, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_src, "traffic": traffic,
                 "algorithmic_bytes_per_launch": kp["bytes"] / kp["launches"],
@@ -477,7 +481,7 @@ def main():
                "config": {"workload": f"{a.lattice} Wilson, m_q={m_q} ({mass_src}, cond(A)~{a.kappa}), "
                                       f"per step 1 eigCG({a.nev},{a.m}) + grow + k={k} batched init-CG, "
                                       f"basis {l0} FP32 vectors, tol {a.tol}, restart {a.restart_tol}",
-                          "lattice": a.lattice, "k": k, "basis": l0, "storage": f"fp32 spinors, {a.links}-real fp32 links, "
+                          "lattice": a.lattice, "k": k, "basis": l0, "storage": "fp32 spinors, fp32 links (12- and 18-real resident, chosen per k by the autotuner), "
                           "double-float residual replacements, fp64 final residual", "l2": "inputs larger than L2 (each field >= 85 MB)",
                           "parallelism": f"replicas{world}"},
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,

@@ -64,7 +64,9 @@ typedef struct eig_basis_s *eig_basis;
 
 typedef struct {
     int spinor_prec;        /* EIG_PREC_*; storage of Krylov vectors and links           */
-    int link_compress12;    /* 1: store two rows per link, rebuild the third (FP32/F16)  */
+    int link_compress12;    /* 1: store two rows per link, rebuild the third (FP32/F16);
+                               FP32 ops also keep the other FP32 form and use, per k,
+                               whichever the stencil autotuner measured faster          */
     int max_rhs;            /* largest k of one batched call (1..16); sizes buffers      */
     double reliable_delta;  /* mixed precision: FP64 residual update when ||r|| falls by
                                this factor since the last one (0 -> 0.1)                  */

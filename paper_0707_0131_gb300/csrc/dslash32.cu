@@ -150,47 +150,90 @@ int d32_grid(const void *kern, long work, int cap, size_t smem) {
 
 bool dslash32_handles(const DslashCall &c) { return c.in.prec != P64; }
 
-// Times the plain stencil in every valid variant on the caller's buffers (in -> out)
-// and caches the fastest for this (V, k, storage, link format).
-cudaError_t autotune_dslash32(const DslashCall &c, cudaStream_t s) {
-    K32 a = args32(c);
-    if (forced_variant() >= 0) return cudaSuccess;
-    const int prec = c.in.prec == P32 ? 32 : 16;
+std::mutex g_fmt_mu;
+std::unordered_map<unsigned long long, int> g_fmt;  // (V, k, prec) -> faster link format
+
+unsigned long long fmt_key(unsigned V, unsigned k, int prec) {
+    return ((unsigned long long)V << 24) ^ ((unsigned long long)k << 8) ^ (unsigned long long)prec;
+}
+
+// EIG_DSLASH_LINKS=12 or 18 in the environment forces the FP32 link format
+int forced_gformat() {
+    static int f = -2;
+    if (f == -2) {
+        const char *e = getenv("EIG_DSLASH_LINKS");
+        f = !e ? -1 : (strcmp(e, "12") == 0 ? GF_F32_12 : (strcmp(e, "18") == 0 ? GF_F32_18 : -1));
+    }
+    return f;
+}
+
+int dslash32_best_gformat(long V, int k, int prec) {
+    if (prec == 32 && forced_gformat() >= 0) return forced_gformat();
+    std::lock_guard<std::mutex> lk(g_fmt_mu);
+    auto it = g_fmt.find(fmt_key((unsigned)V, (unsigned)k, prec));
+    return it == g_fmt.end() ? -1 : it->second;
+}
+
+// Times the plain stencil in every valid variant on the caller's buffers (in -> out),
+// for the call's link format and the alternative one, and caches the fastest choices.
+cudaError_t autotune_dslash32(const DslashCall &c0, const void *const *gauge_alts, const int *gf_alts, int n_alts,
+                              cudaStream_t s) {
+    const int prec = c0.in.prec == P32 ? 32 : 16;
     {
-        std::lock_guard<std::mutex> lk(g_var_mu);
-        if (g_var.count(var_key(a.V, a.k, prec, c.gformat))) return cudaSuccess;
+        std::lock_guard<std::mutex> lk(g_fmt_mu);
+        if (g_fmt.count(fmt_key((unsigned)c0.V, (unsigned)c0.k, prec))) return cudaSuccess;
     }
     const char *le = getenv("EIG_AUTOTUNE_LOG");
     const bool log = le && le[0] == '1';
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    float best = 1e30f;
-    int best_v = -1;
-    for (int v = 0; v < NVAR; v++) {
-        if (!variant_ok(v, a.k, c.gformat)) continue;
-        g_var_override = v;
-        dispatch32<E_PLAIN>(c, a, 0, s);  // warm
-        cudaEventRecord(e0, s);
-        for (int rep = 0; rep < 3; rep++) dispatch32<E_PLAIN>(c, a, 0, s);
-        cudaEventRecord(e1, s);
-        cudaEventSynchronize(e1);
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (log)
-            fprintf(stderr, "dslash32 autotune V=%u k=%u prec=%d gf=%d variant %d: %.4f ms per launch\n", a.V, a.k,
-                    prec, c.gformat, v, ms / 3.0);
-        if (ms < best) {
-            best = ms;
-            best_v = v;
+    float best_fmt_ms = 1e30f;
+    int best_fmt = c0.gformat;
+    for (int f = 0; f <= n_alts; f++) {
+        DslashCall c = c0;
+        if (f >= 1) {
+            if (!gauge_alts[f - 1]) continue;
+            c.gauge.data = const_cast<void *>(gauge_alts[f - 1]);
+            c.gformat = gf_alts[f - 1];
+        }
+        K32 a = args32(c);
+        float best = 1e30f;
+        int best_v = -1;
+        for (int v = 0; v < NVAR; v++) {
+            if (!variant_ok(v, a.k, c.gformat)) continue;
+            if (forced_variant() >= 0 && v != forced_variant()) continue;
+            g_var_override = v;
+            dispatch32<E_PLAIN>(c, a, 0, s);  // warm
+            cudaEventRecord(e0, s);
+            for (int rep = 0; rep < 3; rep++) dispatch32<E_PLAIN>(c, a, 0, s);
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (log)
+                fprintf(stderr, "dslash32 autotune V=%u k=%u prec=%d gf=%d variant %d: %.4f ms per launch\n", a.V,
+                        a.k, prec, c.gformat, v, ms / 3.0);
+            if (ms < best) {
+                best = ms;
+                best_v = v;
+            }
+        }
+        g_var_override = -1;
+        if (best_v >= 0) {
+            std::lock_guard<std::mutex> lk(g_var_mu);
+            g_var[var_key(a.V, a.k, prec, c.gformat)] = best_v;
+        }
+        if (best < best_fmt_ms) {
+            best_fmt_ms = best;
+            best_fmt = c.gformat;
         }
     }
-    g_var_override = -1;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (best_v >= 0) {
-        std::lock_guard<std::mutex> lk(g_var_mu);
-        g_var[var_key(a.V, a.k, prec, c.gformat)] = best_v;
+    {
+        std::lock_guard<std::mutex> lk(g_fmt_mu);
+        g_fmt[fmt_key((unsigned)c0.V, (unsigned)c0.k, prec)] = best_fmt;
     }
     return cudaGetLastError();
 }

@@ -210,7 +210,7 @@ __device__ __forceinline__ void hop(const KD &a, unsigned s, unsigned sf, unsign
 }
 
 template <bool DAG>
-__global__ void __launch_bounds__(128) k_dslash_dd(const KD a) {
+__global__ void __launch_bounds__(128, 3) k_dslash_dd(const KD a) {  // 3 blocks (12 warps) per SM
     __shared__ double smem[(128 / 32) * MAX_RHS];
     const unsigned total = a.V * a.k;
     const unsigned s1 = a.L0, s2 = a.L0 * a.L1, s3 = s2 * a.L2;

@@ -159,6 +159,8 @@ struct eig_op_s {
     int max_rhs;
     double delta;
     DevBuf gauge64, gauge_in, gauge_dd;  // gauge_dd: double-float copy (mixed precision)
+    DevBuf gauge_alt;                    // FP32 ops: the links in the other FP32 format
+    int gf_alt = -1;
     // workspace
     FieldBuf r, p, u, xlo, b64, x64, r64, u64, rsv, xsv;
     DevBuf nat_in, nat_out;
@@ -179,6 +181,8 @@ struct eig_op_s {
         ProfRecord rec;
     };
     std::vector<CgGraph> graphs;
+    DevBuf tcerr;      // error flag of the tensor-core window restart
+    PinBuf errh;
     DevBuf jbase_dev;  // iteration base the replayed kernels add to their offsets
     PinBuf jbase_h;
     cudaStream_t cap_stream = nullptr;  // private stream the graphs are captured on
@@ -204,6 +208,13 @@ struct eig_op_s {
         c.gauge.data = f64 ? gauge64.p : gauge_in.p;
         c.gauge.V = V;
         c.gformat = f64 ? GF_F64_18 : gf_inner;
+        if (!f64 && prec == P32) {
+            const int best = dslash32_best_gformat(V, in.v.k, 32);
+            if (best == gf_alt && gauge_alt.p) {
+                c.gauge.data = gauge_alt.p;
+                c.gformat = gf_alt;
+            }
+        }
         for (int i = 0; i < 4; i++) c.L[i] = L[i];
         c.V = V;
         c.k = in.v.k;
@@ -247,7 +258,7 @@ struct eig_basis_s {
     bool chol_ok = true;
     DevBuf C, Y;            // device small matrices
     DevBuf tcpart, tcerr;   // partial sums and error flag of the tensor-core U^H R
-    PinBuf Ch;
+    PinBuf Ch, errh;
     std::mutex mu;
     long fsize() const { return op->V * 12; }  // complex entries per field
 };
@@ -469,6 +480,9 @@ static void check_breakdown(const Solve &sv) {
         if (sv.sth[q].breakdown) throw Error{EIG_ERR_BREAKDOWN, "CG breakdown (p^H A p <= 0, NaN or Inf)"};
 }
 
+static bool tc_gemm_enabled();
+static ColSet field_cols(void *base, bool f64, int k, long fsize, int ncols, bool rhs_inner);
+
 // Plain CG iterations of init-CG run as replays of a captured graph of CHECK
 // iterations unless kernel timing is on (its events would be captured too) or
 // EIG_CG_GRAPH=0 is set.
@@ -634,12 +648,34 @@ static bool cg_run(Solve &sv, int max_iter, Window *w, eig_op_s *op) {
                 Vw.col_off = op->col_off.as<long>();
                 void *tp = w->tprev_is_a ? op->tprev.p : op->tcur.p;
                 void *tc = w->tprev_is_a ? op->tcur.p : op->tprev.p;
-                CUDA_CK(launch_window_restart(Vw, m, op->qz.as<double>(), nout, tc, tp, sv.h.beta + (size_t)j * k,
-                                              op->ncomplex(), op->wv.as<double>(), sv.red, s));
+                const bool tcw = !Vw.f64 && nout <= 32 && (op->ncomplex() % 2) == 0 && tc_gemm_enabled();
+                if (tcw) {
+                    // V <- V QZ on the tensor cores, in place (each CTA reads all m columns of
+                    // its rows before writing them), then w^H V_new with w = t - beta t_prev
+                    ColSet Out = Vw;
+                    Out.ncols = nout;
+                    op->tcerr.ensure(16);
+                    op->errh.ensure(16);
+                    CUDA_CK(cudaMemsetAsync(op->tcerr.p, 0, 16, s));
+                    CUDA_CK(launch_tc_ay(Vw, op->qz.as<double>(), Out, 0.0, op->ncomplex(), op->tcerr.as<int>(), s));
+                    Field wf = op->rsv.view(1);
+                    CUDA_CK(launch_w_diff(tc, tp, sv.h.beta + (size_t)j * k, wf.v.data, op->ncomplex(), s));
+                    // V_new^H w (nout x 1), conjugated below to w^H V_new
+                    ColSet W1 = field_cols(wf.v.data, false, 1, op->V * 12, 1, false);
+                    CUDA_CK(launch_gemm_ahb(Out, W1, op->ncomplex(), op->wv.as<double>(), sv.red, s));
+                    CUDA_CK(cudaMemcpyAsync(op->errh.p, op->tcerr.p, 4, cudaMemcpyDeviceToHost, s));
+                } else {
+                    CUDA_CK(launch_window_restart(Vw, m, op->qz.as<double>(), nout, tc, tp, sv.h.beta + (size_t)j * k,
+                                                  op->ncomplex(), op->wv.as<double>(), sv.red, s));
+                }
                 // the restart reads qz/col_off asynchronously: keep host vectors alive until done
                 sync(s);
+                if (tcw && *op->errh.as<int>() != 0)
+                    throw Error{EIG_ERR_TIMEOUT, "tensor-core window restart: a bounded wait in the kernel gave up"};
                 std::vector<double> wv(2 * nout);
                 CUDA_CK(cudaMemcpy(wv.data(), op->wv.p, wv.size() * sizeof(double), cudaMemcpyDeviceToHost));
+                if (tcw)
+                    for (int c = 0; c < nout; c++) wv[2 * c + 1] = -wv[2 * c + 1];
                 std::vector<int> newslots(w->slots.begin(), w->slots.begin() + nout);
                 for (int a = nout; a < m; a++) w->freel.push_back(w->slots[a]);
                 newslots.push_back(slot);
@@ -688,7 +724,13 @@ static bool cg_finish(Solve &sv, int max_iter, Window *w, eig_op_s *op, int &ext
 // Picks the stencil variant for this k on the op's own buffers (once per op shape).
 static void tune_for(eig_op_s *op, int k, cudaStream_t s) {
     if (op->prec == P64) return;
-    CUDA_CK(autotune_dslash32(op->call(op->p.view(k), op->u.view(k), false, false), s));
+    // tuned on the primary format's call (call() picks a format only once tuned)
+    DslashCall c = op->call(op->p.view(k), op->u.view(k), false, false);
+    c.gauge.data = op->gauge_in.p;
+    c.gformat = op->gf_inner;
+    const void *alts[1] = {op->gauge_alt.p};
+    const int gfs[1] = {op->gf_alt};
+    CUDA_CK(autotune_dslash32(c, alts, gfs, 1, s));
 }
 
 static Solve make_solve(eig_op_s *op, int k, cudaStream_t s, int max_iter) {
@@ -782,11 +824,11 @@ static void refactor(eig_basis_s *B) {
     B->chol_ok = l == 0 || dense::cholesky(l, B->Lc.data());
 }
 
-// U^H r of the deflation on the tensor cores (FP32 windows): EIG_GEMM_TC=1 in the
-// environment selects it, read at every call.
+// The FP32 contractions of deflation, growth and the eigCG restart run on the tensor
+// cores unless EIG_GEMM_TC=0 is set (read at every call; CUDA-core kernels then).
 static bool tc_gemm_enabled() {
     const char *e = getenv("EIG_GEMM_TC");
-    return e && e[0] == '1';
+    return !(e && e[0] == '0');
 }
 
 // C = A^H B into B->C (device) and B->Ch (host; the stream is synchronised).  FP32
@@ -814,6 +856,23 @@ static const cd *ahb_to_host(eig_basis_s *B, const ColSet &A, const ColSet &Bc, 
     return B->Ch.as<cd>();
 }
 
+// Out = beta Out + A Y; FP32 column sets go to the tensor cores when
+// tc_gemm_enabled(), with the kernel's error flag read back and checked.
+static void ay_run(eig_basis_s *B, const ColSet &A, const double *Y, const ColSet &Out, double beta, long nrow,
+                   cudaStream_t s) {
+    if (tc_gemm_enabled() && (nrow % 2) == 0 && tc_ay_ok(A, Out)) {
+        B->tcerr.ensure(16);
+        B->errh.ensure(16);
+        CUDA_CK(cudaMemsetAsync(B->tcerr.p, 0, 16, s));
+        CUDA_CK(launch_tc_ay(A, Y, Out, beta, nrow, B->tcerr.as<int>(), s));
+        CUDA_CK(cudaMemcpyAsync(B->errh.p, B->tcerr.p, 4, cudaMemcpyDeviceToHost, s));
+        sync(s);
+        if (*B->errh.as<int>() != 0) throw Error{EIG_ERR_TIMEOUT, "tensor-core A Y: a bounded wait in the kernel gave up"};
+        return;
+    }
+    CUDA_CK(launch_gemm_ay(A, Y, Out, beta, nrow, s));
+}
+
 // x64 <- x64 + U H^{-1} U^H r64 for k RHS (r64 given in FP64).
 static void deflate_into(eig_basis_s *B, Field r64, Field x64, cudaStream_t s) {
     eig_op_s *op = B->op;
@@ -837,7 +896,7 @@ static void deflate_into(eig_basis_s *B, Field r64, Field x64, cudaStream_t s) {
     CUDA_CK(cudaMemcpyAsync(B->Y.p, Yr.data(), Yr.size() * 16, cudaMemcpyHostToDevice, s));
     Field xsv = op->xsv.view(k);
     ColSet X = field_cols(xsv.v.data, f64, k, B->fsize(), k, true);
-    CUDA_CK(launch_gemm_ay(basis_cols(B, 0, l), B->Y.as<double>(), X, 0.0, op->ncomplex(), s));
+    ay_run(B, basis_cols(B, 0, l), B->Y.as<double>(), X, 0.0, op->ncomplex(), s);
     CUDA_CK(launch_combine(x64, 1.0, x64, 1.0, xsv, s));
     sync(s);  // Yr must outlive the async copy
 }
@@ -936,6 +995,13 @@ eig_status eig_op_create(const double *gauge, const int dims[4], double m_q, con
         size_t gb = op->gf_inner == GF_F32_12 ? 48 : (op->gf_inner == GF_F32_18 ? 72 : 24);
         op->gauge_in.alloc((size_t)V * 4 * gb);
         CUDA_CK(launch_pack_gauge(stage.as<double>(), op->gauge_in.p, op->gf_inner, V, 0));
+        if (op->prec == P32) {
+            // the other FP32 link format as well: 12 reals win where the stencil is
+            // memory bound (few RHS), 18 reals where it is issue bound (many RHS)
+            op->gf_alt = op->gf_inner == GF_F32_12 ? GF_F32_18 : GF_F32_12;
+            op->gauge_alt.alloc((size_t)V * 4 * (op->gf_alt == GF_F32_12 ? 48 : 72));
+            CUDA_CK(launch_pack_gauge(stage.as<double>(), op->gauge_alt.p, op->gf_alt, V, 0));
+        }
     }
     CUDA_CK(cudaDeviceSynchronize());
     // workspace
@@ -1135,7 +1201,7 @@ eig_status eig_eigcg_solve(eig_op op, eig_basis basis, const double *b, double *
             A.ncols = w.i;
             A.col_off = op->col_off.as<long>();
             ColSet O = field_cols(basis->pend.p, A.f64, 1, basis->fsize(), nr, false);
-            CUDA_CK(launch_gemm_ay(A, basis->Y.as<double>(), O, 0.0, op->ncomplex(), s));
+            ay_run(basis, A, basis->Y.as<double>(), O, 0.0, op->ncomplex(), s);
             sync(s);
             basis->npend = nr;
             basis->pend_ritz = ev;
@@ -1185,7 +1251,7 @@ eig_status eig_basis_grow(eig_basis B, void *stream) {
             for (size_t q = 0; q < negc.size(); q++) negc[q] = -c[q];
             B->Y.ensure(negc.size() * sizeof(double));
             CUDA_CK(cudaMemcpyAsync(B->Y.p, negc.data(), negc.size() * sizeof(double), cudaMemcpyHostToDevice, s));
-            CUDA_CK(launch_gemm_ay(basis_cols(B, 0, l), B->Y.as<double>(), P, 1.0, nrow, s));
+            ay_run(B, basis_cols(B, 0, l), B->Y.as<double>(), P, 1.0, nrow, s);
             sync(s);
         }
     }
@@ -1211,7 +1277,7 @@ eig_status eig_basis_grow(eig_basis B, void *stream) {
         }
     B->Y.ensure(yr.size() * sizeof(double));
     CUDA_CK(cudaMemcpyAsync(B->Y.p, yr.data(), yr.size() * sizeof(double), cudaMemcpyHostToDevice, s));
-    CUDA_CK(launch_gemm_ay(P, B->Y.as<double>(), basis_cols(B, l, r), 0.0, nrow, s));
+    ay_run(B, P, B->Y.as<double>(), basis_cols(B, l, r), 0.0, nrow, s);
     {
         // second pass: the remainders can be nearly dependent, so orthonormalise again
         ColSet Un = basis_cols(B, l, r);
@@ -1228,8 +1294,7 @@ eig_status eig_basis_grow(eig_basis B, void *stream) {
                 y2[((size_t)a * r + c) * 2 + 1] = R2[(size_t)c * r + a].imag();
             }
         CUDA_CK(cudaMemcpyAsync(B->Y.p, y2.data(), y2.size() * sizeof(double), cudaMemcpyHostToDevice, s));
-        CUDA_CK(launch_gemm_ay(Un, B->Y.as<double>(), field_cols(B->pend.p, f64, 1, B->fsize(), r, false), 0.0,
-                               nrow, s));
+        ay_run(B, Un, B->Y.as<double>(), field_cols(B->pend.p, f64, 1, B->fsize(), r, false), 0.0, nrow, s);
         CUDA_CK(cudaMemcpyAsync((char *)B->U.p + (size_t)l * op->wfield_bytes(), B->pend.p,
                                 (size_t)r * op->wfield_bytes(), cudaMemcpyDeviceToDevice, s));
         sync(s);
@@ -1408,7 +1473,7 @@ eig_status eig_basis_ritz(eig_basis B, double *evals, double *resnorms, int *n, 
         B->Y.ensure(yr.size() * sizeof(double));
         CUDA_CK(cudaMemcpyAsync(B->Y.p, yr.data(), yr.size() * sizeof(double), cudaMemcpyHostToDevice, s));
         ColSet Wc = field_cols(B->W.p, f64, 1, B->fsize(), nc, false);
-        CUDA_CK(launch_gemm_ay(basis_cols(B, 0, l), B->Y.as<double>(), Wc, 0.0, op->ncomplex(), s));
+        ay_run(B, basis_cols(B, 0, l), B->Y.as<double>(), Wc, 0.0, op->ncomplex(), s);
         for (int c = 0; c < nc; c++) {
             Field wc = field_at(op->wprec, (char *)B->W.p + (size_t)c * op->wfield_bytes(), op->V, 1);
             CUDA_CK(launch_combine(x64, 1.0, wc, 0.0, null_field(), s));

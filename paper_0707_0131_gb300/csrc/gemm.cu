@@ -648,4 +648,31 @@ cudaError_t launch_window_restart(ColSet Vw, int m, const double *QZ, int nout, 
     return cudaGetLastError();
 }
 
+// w = t - beta t_prev (FP32 fields of one RHS; beta read from the device): the vector
+// A z_j of Fig. 1 step 11.8 whose dot products with the restarted window form the new
+// row of T.
+namespace {
+__global__ void k_w_diff(const float4 *__restrict__ t, const float4 *__restrict__ tp, const double *beta_dev,
+                         float4 *__restrict__ w, long n4) {
+    const float b = (float)(*beta_dev);
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (long)gridDim.x * blockDim.x) {
+        const float4 x = t[i], y = tp[i];
+        w[i] = make_float4(x.x - b * y.x, x.y - b * y.y, x.z - b * y.z, x.w - b * y.w);
+    }
+}
+}  // namespace
+
+cudaError_t launch_w_diff(const void *t, const void *t_prev, const double *beta_dev, void *w, long n_complex,
+                          cudaStream_t s) {
+    if (n_complex % 2) return cudaErrorInvalidValue;
+    ProfScope prof("w_diff", (double)n_complex * 24.0, s);
+    const long n4 = n_complex / 2;
+    long grid = (n4 + 255) / 256;
+    const long cap = (long)device_sm_count() * 8;
+    if (grid > cap) grid = cap;
+    k_w_diff<<<(int)grid, 256, 0, s>>>(static_cast<const float4 *>(t), static_cast<const float4 *>(t_prev), beta_dev,
+                                       static_cast<float4 *>(w), n4);
+    return cudaGetLastError();
+}
+
 }  // namespace eig

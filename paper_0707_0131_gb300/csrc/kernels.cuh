@@ -91,7 +91,13 @@ cudaError_t launch_dslash32_norm(const DslashCall &c, CGScalars *st, History h, 
 cudaError_t launch_dslash32_cg(const DslashCall &c, Field r, Field t_save, CGScalars *st, History h, int iter,
                                RedScratch red, cudaStream_t s);
 // chooses (once per volume, k and format) how many RHS each stencil thread handles
-cudaError_t autotune_dslash32(const DslashCall &c, cudaStream_t s);
+// Times every stencil variant on c's buffers (in -> out), for c's link format and for
+// the same links stored in each of the n_alts other formats gf_alts (data gauge_alts);
+// caches the fastest variant per format and the fastest format for (V, k, storage).
+cudaError_t autotune_dslash32(const DslashCall &c, const void *const *gauge_alts, const int *gf_alts, int n_alts,
+                              cudaStream_t s);
+// The link format the autotuner found faster for (V, k, storage), or -1 if not tuned.
+int dslash32_best_gformat(long V, int k, int prec);
 
 // dslash_dd.cu: double-float (FP32-pair) stencil for residual replacements.  dd fields
 // have the FP64 layout with float4 (re_hi, im_hi, re_lo, im_lo) per complex number.
@@ -162,6 +168,20 @@ cudaError_t launch_window_restart(ColSet Vw, int m, const double *QZ, int nout, 
 bool tc_ahb_ok(const ColSet &A, const ColSet &B);
 size_t tc_ahb_partials_bytes(long nrows, int l, int k);
 cudaError_t launch_tc_ahb(const ColSet &A, const ColSet &B, long nrows, double *C, double *partials, int *err,
+                          cudaStream_t s);
+
+// Out = beta Out + A Y on the tensor cores (kind::tf32, hi/lo split operands; K = 2 nA
+// <= 1024 accumulated in one TMEM accumulator per 128-row tile).  A: FP32 fields, one
+// per column (col_stride or even col_off offsets), nA <= 512; Out: FP32, nOut <= 16
+// columns, RHS-inner or one field per column, not overlapping A; Y: FP64 complex
+// nA x nOut row-major on the device; nrows even.  *err (device, zeroed by the caller)
+// becomes non-zero if a bounded wait gave up (Out is then invalid).
+bool tc_ay_ok(const ColSet &A, const ColSet &Out);
+cudaError_t launch_tc_ay(const ColSet &A, const double *Y, const ColSet &Out, double beta, long nrows, int *err,
+                         cudaStream_t s);
+
+// w = t - (*beta_dev) t_prev for FP32 fields of n_complex entries (n_complex even)
+cudaError_t launch_w_diff(const void *t, const void *t_prev, const double *beta_dev, void *w, long n_complex,
                           cudaStream_t s);
 
 int device_sm_count();

@@ -19,11 +19,11 @@
 // double-float (TwoSum) sums while the next group accumulates.  Each CTA writes
 // its sums as FP64 partials; a second kernel adds the partials in a fixed order.
 //
-// Pipeline per CTA (128 threads): thread 0 issues the TMA loads of up to STAGES
-// K tiles ahead; all threads split the A tile in place and build the B tile;
-// thread 0 issues the MMAs and commits them to the stage's "empty" barrier.
-// Every wait is bounded: on timeout the CTA records an error, drains its copies
-// (bounded), frees its TMEM and returns.
+// Roles per CTA (320 threads): one lane of warp 0 keeps the TMA ring full, one lane
+// of warp 1 issues the MMAs, warps 2..9 split the tiles and drain the accumulators;
+// they hand stages and TMEM regions to each other through mbarriers.  Every wait is
+// bounded: on timeout the CTA records an error, lets its copies land (bounded), frees
+// its TMEM and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -40,8 +40,6 @@ namespace {
 
 constexpr int KT = 32;            // K floats per tile: one 128-byte swizzle row
 constexpr int TM = 128;           // M rows per tile
-constexpr int STAGES = 3;
-constexpr int THREADS = 128;
 constexpr int MAX_CHUNK = 1 << 20;  // K tiles per CTA at most (no cap unless EIG_TC_CHUNK)
 constexpr uint64_t WAIT_NS = 2000000000ull;  // 2 s
 
@@ -52,6 +50,9 @@ __device__ __forceinline__ void mbar_init(uint64_t *b, unsigned count) {
 }
 __device__ __forceinline__ void mbar_expect_tx(uint64_t *b, unsigned bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(sa(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(sa(b)) : "memory");
 }
 __device__ __forceinline__ bool mbar_try(uint64_t *b, unsigned phase) {
     uint32_t ok;
@@ -149,56 +150,75 @@ __device__ __forceinline__ void two_sum_add(float &hi, float &lo, float x) {
     lo = __fadd_rn(lo, err);
 }
 
-// D regions: two TMEM accumulators of MT * N columns used by alternate groups of
-// FLUSH K tiles; a group's result is drained into per-thread double-float sums
-// while the next group accumulates in the other region.  The tensor pipe adds in
-// FP32 with its own rounding, so its error grows with the accumulation length:
-// draining every FLUSH tiles keeps the result at FP32-product accuracy.
+// Warp specialisation: warp 0 (one lane) keeps the TMA ring full, warp 1 (one lane)
+// issues the MMAs, warps 2..9 split the A tiles in place into hi / lo, build the B
+// tiles and drain the accumulators.  The roles hand stages and TMEM regions to each
+// other through mbarriers only, so no role waits for work that was issued just
+// before (a block-wide barrier per tile made every tile cost one MMA round trip).
+//
+// Accumulation: groups of FLUSH K tiles accumulate in one of NREG TMEM regions (MT * N
+// columns each).  The tensor pipe adds in FP32 with its own rounding, so its error
+// grows with the accumulation length; each finished group is drained into per-thread
+// double-float sums, two groups behind the MMAs, and its region is then reused.
 constexpr int FLUSH = 2;
+constexpr int NREG = 3;
+constexpr int WORKERS = 8;                    // worker warps
+constexpr int TC_THREADS = 32 * (2 + WORKERS);
+static_assert((KT / 2) * 16 <= 32 * WORKERS, "one B value per worker thread per tile for k <= 16");
 
+// Worker warp w (warps 2..9) drains TMEM lanes 32 (w % 4) .. + 31 (the lane quarter a
+// warp may access) and the half h = (w - 2) / 4 of the region's MT * N columns.
 template <int MT, int N>
-__device__ __forceinline__ void drain(uint32_t region, int warp, float *acc_hi, float *acc_lo) {
+__device__ __forceinline__ void drain(uint32_t region, int quarter, int half, float *acc_hi, float *acc_lo) {
+    constexpr int HC = MT * N / 2;
+    const uint32_t base = region + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * HC);
 #pragma unroll
-    for (int c0 = 0; c0 < MT * N; c0 += 16) {
-        uint32_t v[16];
-        const uint32_t addr = region + ((uint32_t)(warp * 32) << 16) + c0;
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-            "[%16];\n"
-            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-            : "r"(addr)
-            : "memory");
+    for (int c0 = 0; c0 < HC; c0 += 8) {
+        uint32_t v[8];
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+                     : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                     : "r"(base + c0)
+                     : "memory");
         asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
-        for (int j = 0; j < 16; j++) two_sum_add(acc_hi[c0 + j], acc_lo[c0 + j], __uint_as_float(v[j]));
+        for (int j = 0; j < 8; j++) two_sum_add(acc_hi[c0 + j], acc_lo[c0 + j], __uint_as_float(v[j]));
     }
 }
 
-template <int MT, int N>
-__global__ void __launch_bounds__(THREADS, 1) k_tc_ahb(const __grid_constant__ CUtensorMap tmap, const TcArgs a) {
+template <int MT, int N, int NS>
+__global__ void __launch_bounds__(TC_THREADS, 1) k_tc_ahb(const __grid_constant__ CUtensorMap tmap, const TcArgs a) {
     extern __shared__ __align__(1024) unsigned char sm_raw[];
-    // 1024-byte aligned stage buffers: [MT] A_hi tiles, [MT] A_lo tiles, B_hi, B_lo
+    // 1024-byte aligned stages: [MT] A tiles (TMA lands here, split in place to hi),
+    // [MT] A_lo tiles, B_hi, B_lo
     unsigned char *base = sm_raw + ((1024 - (sa(sm_raw) & 1023)) & 1023);
     constexpr uint32_t a_bytes = TM * KT * 4;  // 16 KB
     constexpr uint32_t b_bytes = (uint32_t)((N + 7) / 8) * 1024;
     constexpr uint32_t stage_bytes = 2 * MT * a_bytes + 2 * b_bytes;
-    constexpr uint32_t NCOLS = 2 * MT * N <= 32 ? 32 : (2 * MT * N <= 64 ? 64 : 128);
-    __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], dfull[2], done;
+    constexpr uint32_t RCOLS = MT * N;
+    constexpr uint32_t NCOLS = NREG * RCOLS <= 32 ? 32 : (NREG * RCOLS <= 64 ? 64 : (NREG * RCOLS <= 128 ? 128 : 256));
+    __shared__ __align__(8) uint64_t raw_full[NS], split_done[NS], stage_free[NS], acc_full[NREG], acc_empty[NREG],
+        done;
     __shared__ uint32_t tmem_base;
-    __shared__ int abort_flag;
+    __shared__ volatile int abort_flag;
+    __shared__ int n_issued, n_consumed;
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     const int kt0 = blockIdx.x * a.chunk;
     const int nkt = min(a.chunk, a.ktiles - kt0);
+    const int ngroups = (nkt + FLUSH - 1) / FLUSH;
     if (t == 0) {
-        for (int s = 0; s < STAGES; s++) {
-            mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 1);
+        for (int s = 0; s < NS; s++) {
+            mbar_init(&raw_full[s], 1);
+            mbar_init(&split_done[s], WORKERS);
+            mbar_init(&stage_free[s], 1);
         }
-        mbar_init(&dfull[0], 1);
-        mbar_init(&dfull[1], 1);
+        for (int r = 0; r < NREG; r++) {
+            mbar_init(&acc_full[r], 1);
+            mbar_init(&acc_empty[r], WORKERS);
+        }
         mbar_init(&done, 1);
         abort_flag = 0;
+        n_issued = 0;
+        n_consumed = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     if (warp == 0) {
@@ -210,141 +230,165 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_ahb(const __grid_constant__ C
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     const uint32_t tmem = tmem_base;
-    auto region = [&](int g) { return tmem + (uint32_t)((g & 1) * MT * N); };
+    auto region = [&](int g) { return tmem + (uint32_t)((g % NREG) * RCOLS); };
     auto A_hi = [&](int s, int mt) { return base + s * stage_bytes + mt * a_bytes; };
     auto A_lo = [&](int s, int mt) { return base + s * stage_bytes + (MT + mt) * a_bytes; };
     auto B_hi = [&](int s) { return base + s * stage_bytes + 2 * MT * a_bytes; };
     auto B_lo = [&](int s) { return base + s * stage_bytes + 2 * MT * a_bytes + b_bytes; };
-    auto issue = [&](int kt) {  // thread 0 only
-        const int s = kt % STAGES;
-        mbar_expect_tx(&full[s], MT * a_bytes);
-        for (int mt = 0; mt < MT; mt++) tma_load_2d(A_hi(s, mt), &tmap, (kt0 + kt) * KT, mt * TM, &full[s]);
+    auto fail = [&](int code) {
+        atomicExch(a.err, code);
+        abort_flag = 1;
     };
-    float acc_hi[MT * N], acc_lo[MT * N];
-#pragma unroll
-    for (int c = 0; c < MT * N; c++) acc_hi[c] = acc_lo[c] = 0.f;
-    int issued = 0;
-    if (t == 0)
-        for (; issued < STAGES - 1 && issued < nkt; issued++) issue(issued);
-    const uint32_t idesc = idesc_tf32(TM, N);
-    int consumed = 0;
-    for (int kt = 0; kt < nkt; kt++) {
-        const int s = kt % STAGES;
-        if (!mbar_wait(&full[s], (kt / STAGES) & 1)) {
-            atomicExch(a.err, 2);
-            abort_flag = 1;
-        }
-        __syncthreads();
-        if (abort_flag) break;
-        consumed = kt + 1;
-        // split A in place: hi (low mantissa bits cleared), lo = x - hi
-        for (int mt = 0; mt < MT; mt++) {
-            float4 *ah = reinterpret_cast<float4 *>(A_hi(s, mt));
-            float4 *al = reinterpret_cast<float4 *>(A_lo(s, mt));
-            for (int i = t; i < TM * KT / 4; i += THREADS) {
-                const float4 v = ah[i];
-                const float4 h = make_float4(hi_tf32(v.x), hi_tf32(v.y), hi_tf32(v.z), hi_tf32(v.w));
-                ah[i] = h;
-                al[i] = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+
+    if (warp == 0) {
+        // ---------------- producer: TMA loads of the A tiles ----------------
+        if (lane == 0) {
+            int kt = 0;
+            for (; kt < nkt && !abort_flag; kt++) {
+                const int s = kt % NS;
+                if (kt >= NS && !mbar_wait(&stage_free[s], ((kt / NS) - 1) & 1)) {
+                    fail(1);
+                    break;
+                }
+                mbar_expect_tx(&raw_full[s], MT * a_bytes);
+                for (int mt = 0; mt < MT; mt++) tma_load_2d(A_hi(s, mt), &tmap, (kt0 + kt) * KT, mt * TM, &raw_full[s]);
             }
+            n_issued = kt;
         }
-        // B tile: rows c (B1) and k + c (B2), K positions 2n' and 2n' + 1 for complex row n'
-        {
-            const long n0 = (long)(kt0 + kt) * (KT / 2);
+    } else if (warp == 1) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            const uint32_t idesc = idesc_tf32(TM, N);
+            for (int kt = 0; kt < nkt && !abort_flag; kt++) {
+                const int s = kt % NS, g = kt / FLUSH;
+                if (!mbar_wait(&split_done[s], (kt / NS) & 1)) {
+                    fail(2);
+                    break;
+                }
+                if (kt % FLUSH == 0 && g >= NREG && !mbar_wait(&acc_empty[g % NREG], ((g / NREG) - 1) & 1)) {
+                    fail(3);
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                // descriptors of the stage's tiles; a K step of 8 tf32 (32 bytes along the
+                // swizzled row) adds 2 to the start-address field
+                const uint64_t bh0 = sdesc(sa(B_hi(s))), bl0 = sdesc(sa(B_lo(s)));
+#pragma unroll
+                for (int mt = 0; mt < MT; mt++) {
+                    const uint32_t d = region(g) + mt * N;
+                    const uint64_t ah0 = sdesc(sa(A_hi(s, mt))), al0 = sdesc(sa(A_lo(s, mt)));
+#pragma unroll
+                    for (int ks = 0; ks < KT / 8; ks++) {
+                        const uint64_t o = 2 * ks;
+                        mma_tf32(d, ah0 + o, bh0 + o, idesc, (kt % FLUSH != 0 || ks > 0) ? 1 : 0);
+                        mma_tf32(d, ah0 + o, bl0 + o, idesc, 1);
+                        mma_tf32(d, al0 + o, bh0 + o, idesc, 1);
+                    }
+                }
+                mma_commit(&stage_free[s]);
+                if (kt % FLUSH == FLUSH - 1 || kt == nkt - 1) mma_commit(&acc_full[g % NREG]);
+            }
+            mma_commit(&done);  // arrives once every MMA issued above has completed
+        }
+    } else {
+        // ---------------- workers: split A, build B, drain ----------------
+        const int wt = t - 64, quarter = warp & 3, half = (warp - 2) >> 2;
+        constexpr int HC = MT * N / 2;
+        float acc_hi[HC], acc_lo[HC];
+#pragma unroll
+        for (int c = 0; c < HC; c++) acc_hi[c] = acc_lo[c] = 0.f;
+        // B values: worker thread wt < 16 k takes (row np, column c) of each tile; its value
+        // for the next tile is loaded one tile ahead
+        const int bnp = a.ki == 1 ? wt % (KT / 2) : wt / max(a.k, 1);
+        const int bc = a.ki == 1 ? wt / (KT / 2) : wt % max(a.k, 1);
+        const bool bth = wt < (KT / 2) * a.k;
+        auto load_b = [&](int kt) {
+            float2 v = make_float2(0.f, 0.f);
+            const long n = (long)(kt0 + kt) * (KT / 2) + bnp;
+            if (bth && kt < nkt && n < a.nrows)
+                v = a.R[((n >> 1) * a.ki + bc % a.ki) * 2 + (n & 1) + (long)(bc / a.ki) * a.bcol];
+            return v;
+        };
+        auto drain_group = [&](int g) {  // warp-uniform
+            const bool ok = __all_sync(0xffffffffu, mbar_wait(&acc_full[g % NREG], (g / NREG) & 1));
+            if (!ok) {
+                fail(4);
+                return false;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            drain<MT, N>(region(g), quarter, half, acc_hi, acc_lo);
+            asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[g % NREG]);
+            return true;
+        };
+        float2 bcur = load_b(0);
+        int kt = 0;
+        bool ok = true;
+        for (; kt < nkt && ok && !abort_flag; kt++) {
+            const int s = kt % NS, g = kt / FLUSH;
+            const float2 bnext = load_b(kt + 1);
+            if (!__all_sync(0xffffffffu, mbar_wait(&raw_full[s], (kt / NS) & 1))) {
+                fail(5);
+                break;
+            }
+            // split A in place: hi (low mantissa bits cleared), lo = x - hi
+            for (int mt = 0; mt < MT; mt++) {
+                float4 *ah = reinterpret_cast<float4 *>(A_hi(s, mt));
+                float4 *al = reinterpret_cast<float4 *>(A_lo(s, mt));
+                for (int i = wt; i < TM * KT / 4; i += 32 * WORKERS) {
+                    const float4 v = ah[i];
+                    const float4 h = make_float4(hi_tf32(v.x), hi_tf32(v.y), hi_tf32(v.z), hi_tf32(v.w));
+                    ah[i] = h;
+                    al[i] = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+                }
+            }
+            // B tile: rows c (B1) and k + c (B2), K positions 2n' and 2n' + 1 for complex row n'
             unsigned char *bh = B_hi(s), *bl = B_lo(s);
-            for (int i = 2 * a.k * KT + t; i < N * KT; i += THREADS) {  // zero padding rows
+            for (int i = 2 * a.k * KT + wt; i < N * KT; i += 32 * WORKERS) {  // zero padding rows
                 const int r = i / KT, e = i % KT;
                 *reinterpret_cast<float *>(bh + sw128(r, e)) = 0.f;
                 *reinterpret_cast<float *>(bl + sw128(r, e)) = 0.f;
             }
-            for (int i = t; i < (KT / 2) * a.k; i += THREADS) {
-                // consecutive threads take consecutive addresses: RHS first in an RHS-inner
-                // field, rows first when each column is a field of its own
-                const int np = a.ki == 1 ? i % (KT / 2) : i / a.k;
-                const int c = a.ki == 1 ? i / (KT / 2) : i % a.k;
-                const long n = n0 + np;
-                float2 v = make_float2(0.f, 0.f);
-                if (n < a.nrows) v = a.R[((n >> 1) * a.ki + c % a.ki) * 2 + (n & 1) + (long)(c / a.ki) * a.bcol];
-                const float vals[4] = {v.x, v.y, v.y, -v.x};  // B1 (re, im), B2 (im, -re)
+            if (bth) {
+                const float vals[4] = {bcur.x, bcur.y, bcur.y, -bcur.x};  // B1 (re, im), B2 (im, -re)
+#pragma unroll
                 for (int q = 0; q < 4; q++) {
-                    const int r = q < 2 ? c : a.k + c;
-                    const int e = 2 * np + (q & 1);
+                    const int r = q < 2 ? bc : a.k + bc;
+                    const int e = 2 * bnp + (q & 1);
                     const float h = hi_tf32(vals[q]);
                     *reinterpret_cast<float *>(bh + sw128(r, e)) = h;
                     *reinterpret_cast<float *>(bl + sw128(r, e)) = vals[q] - h;
                 }
             }
+            bcur = bnext;
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&split_done[s]);
+            // drain the group two behind the one this tile starts
+            if (kt % FLUSH == 0 && g >= 2) ok = drain_group(g - 2);
         }
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        __syncthreads();
-        const int g = kt / FLUSH;
-        if (t == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-            for (int mt = 0; mt < MT; mt++) {
-                const uint32_t d = region(g) + mt * N;
-                for (int ks = 0; ks < KT / 8; ks++) {
-                    const uint32_t off = ks * 32;  // 8 tf32 = 32 bytes along the swizzled row
-                    const uint64_t ah = sdesc(sa(A_hi(s, mt)) + off), al = sdesc(sa(A_lo(s, mt)) + off);
-                    const uint64_t bh = sdesc(sa(B_hi(s)) + off), bl = sdesc(sa(B_lo(s)) + off);
-                    const int acc0 = (kt % FLUSH != 0 || ks > 0) ? 1 : 0;
-                    mma_tf32(d, ah, bh, idesc, acc0);
-                    mma_tf32(d, ah, bl, idesc, 1);
-                    mma_tf32(d, al, bh, idesc, 1);
-                }
-            }
-            mma_commit(&empty[s]);
-            if (kt % FLUSH == FLUSH - 1 || kt == nkt - 1) mma_commit(&dfull[g & 1]);
-            // refill: tile kt + STAGES - 1 goes to the stage of tile kt - 1, whose MMAs
-            // were issued one iteration ago
-            if (issued < nkt) {
-                if (issued >= STAGES && !mbar_wait(&empty[issued % STAGES], ((issued / STAGES) - 1) & 1)) {
-                    atomicExch(a.err, 1);
-                    abort_flag = 1;
-                } else {
-                    issue(issued);
-                    issued++;
+        if (wt == 0) n_consumed = kt;
+        if (ok && kt == nkt && !abort_flag) {
+            // the last two groups
+            for (int g = max(0, ngroups - 2); g < ngroups && ok; g++) ok = drain_group(g);
+            if (ok) {
+                double *P = a.partials + (long)blockIdx.x * MT * TM * N;
+#pragma unroll
+                for (int j = 0; j < HC; j++) {
+                    const int col = half * HC + j;  // TMEM column within the region: mt * N + c
+                    const int row = (col / N) * TM + quarter * 32 + lane;
+                    P[(long)row * N + col % N] = (double)acc_hi[j] + (double)acc_lo[j];
                 }
             }
         }
-        __syncwarp();
-        // at the first tile of group g, the previous group's region is complete: drain it
-        if (kt % FLUSH == 0 && g >= 1) {
-            // tcgen05.ld is warp-collective: the warp drains only if all its lanes saw the group complete
-            const bool ok = __all_sync(0xffffffffu, mbar_wait(&dfull[(g - 1) & 1], ((g - 1) >> 1) & 1));
-            if (!ok) {
-                atomicExch(a.err, 4);
-                abort_flag = 1;
-            } else {
-                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-                drain<MT, N>(region(g - 1), warp, acc_hi, acc_lo);
-            }
-            asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-        }
-    }
-    // after an abort, let the loads still in flight land before the CTA exits
-    if (t == 0)
-        for (int j = consumed; j < issued; j++) mbar_wait(&full[j % STAGES], (j / STAGES) & 1);
-    // all MMAs done
-    if (t == 0) mma_commit(&done);
-    __syncwarp();
-    if (!mbar_wait(&done, 0)) {
-        atomicExch(a.err, 3);
-        abort_flag = 1;
     }
     __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    if (!abort_flag) {
-        // the last group has not been drained yet
-        drain<MT, N>(region((nkt - 1) / FLUSH), warp, acc_hi, acc_lo);
-        double *P = a.partials + (long)blockIdx.x * MT * TM * N;
-#pragma unroll
-        for (int mt = 0; mt < MT; mt++) {
-            const int row = mt * TM + warp * 32 + lane;
-#pragma unroll
-            for (int c = 0; c < N; c++)
-                P[(long)row * N + c] = (double)acc_hi[mt * N + c] + (double)acc_lo[mt * N + c];
-        }
+    if (t == 0) {
+        // after an abort: let the loads still in flight land, and every MMA complete
+        for (int j = n_consumed; j < n_issued; j++) mbar_wait(&raw_full[j % NS], (j / NS) & 1);
     }
+    if (!mbar_wait(&done, 0)) atomicExch(a.err, 6);
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     if (warp == 0)
@@ -365,6 +409,314 @@ __global__ void k_tc_reduce(const double *partials, int grid, int MT, int N, int
     }
     C[2 * idx] = re;
     C[2 * idx + 1] = im;
+}
+
+// ------------------------------------------------------------------------------------
+// Out = beta Out + A Y on the tensor cores (the U y of Eq. 1 and the basis updates of
+// the growth step): D[n, (c, e)] = sum over K = (a, e') of A'[n, K] Yt[K, (c, e)], with
+// M = 128 complex rows per tile, K = 2 * 16 basis columns per chunk (re, im of each)
+// and N = 2k interleaved (re, im) output columns.  Each 1 KB column segment of A is
+// brought into shared memory by a bulk copy (a 3-deep ring, so that the copies of the
+// next chunks are in flight), then transposed to the K-major 128-byte-swizzled layout
+// the MMA reads while being split into TF32 hi and lo parts.  Yt is rebuilt per
+// chunk from Y (FP64 -> FP32 -> hi, lo).  K <= 512, so one TMEM accumulator per tile
+// stays at FP32-product accuracy without draining.
+// ------------------------------------------------------------------------------------
+template <int N>
+struct AyStages {
+    static constexpr int value = N <= 32 ? 6 : 5;  // staging ring depth (bulk copies in flight)
+};
+constexpr int AY_NOP = 3;         // operand (A hi/lo + B hi/lo) buffers
+constexpr int AY_COLS = 16;       // basis columns per K chunk
+constexpr int AY_THREADS = TC_THREADS;
+
+struct AyArgs {
+    const float2 *A;
+    const long *aoff;  // column offsets (complex units) or null: column a at a * acol
+    long acol;
+    int nA;
+    const double *Y;   // nA x k complex, row-major
+    float2 *Out;       // (row n, column c) at ((n >> 1) * oki + c % oki) * 2 + (n & 1) + (c / oki) * ocol,
+    int oki;           // or at ooff[c] + n when ooff is given (oki = 1)
+    long ocol;
+    const long *ooff;
+    int k;
+    float beta;
+    long nrows;
+    int mtiles, nch;   // M tiles, K chunks
+    int *err;
+};
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(sa(dst)),
+        "l"(src), "r"(bytes), "r"(sa(bar))
+        : "memory");
+}
+
+// Same roles as k_tc_ahb: warp 0 issues the bulk copies, warp 1 the MMAs, warps 2..9
+// transpose / split the staged columns, build Yt and write the outputs of each tile
+// one chunk after its last MMA (two TMEM accumulators alternate between tiles).
+template <int N>
+__global__ void __launch_bounds__(AY_THREADS, 1) k_tc_ay(const AyArgs a) {
+    constexpr int AY_NSTG = AyStages<N>::value;
+    extern __shared__ __align__(1024) unsigned char sm_raw[];
+    unsigned char *base = sm_raw + ((1024 - (sa(sm_raw) & 1023)) & 1023);
+    constexpr uint32_t stg_bytes = AY_COLS * TM * 8;            // 16 KB: [16 columns][128 rows] float2
+    constexpr uint32_t a_bytes = TM * KT * 4;                    // 16 KB: one of A_hi / A_lo
+    constexpr uint32_t b_bytes = (uint32_t)(N / 8) * 1024;
+    constexpr uint32_t op_bytes = 2 * a_bytes + 2 * b_bytes;     // A_hi, A_lo, B_hi, B_lo
+    constexpr uint32_t ACOLS = N <= 32 ? 32 : 64;                 // TMEM columns per accumulator
+    unsigned char *stg = base;
+    unsigned char *ops = base + AY_NSTG * stg_bytes;
+    __shared__ __align__(8) uint64_t stg_full[AY_NSTG], stg_free[AY_NSTG], op_ready[AY_NOP], op_free[AY_NOP],
+        acc_full[2], acc_empty[2], done;
+    __shared__ uint32_t tmem_base;
+    __shared__ volatile int abort_flag;
+    __shared__ int n_issued, n_consumed;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int my_tiles = a.mtiles > (int)blockIdx.x ? (a.mtiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const int njobs = my_tiles * a.nch;
+    if (t == 0) {
+        for (int i = 0; i < AY_NSTG; i++) {
+            mbar_init(&stg_full[i], 1);
+            mbar_init(&stg_free[i], WORKERS);
+        }
+        for (int i = 0; i < AY_NOP; i++) {
+            mbar_init(&op_ready[i], WORKERS);
+            mbar_init(&op_free[i], 1);
+        }
+        for (int i = 0; i < 2; i++) {
+            mbar_init(&acc_full[i], 1);
+            mbar_init(&acc_empty[i], WORKERS);
+        }
+        mbar_init(&done, 1);
+        abort_flag = 0;
+        n_issued = 0;
+        n_consumed = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(sa(&tmem_base)),
+                     "r"(2 * ACOLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t tmem = tmem_base;
+    auto job_tile = [&](int j) { return (int)blockIdx.x + (j / a.nch) * (int)gridDim.x; };
+    auto fail = [&](int code) {
+        atomicExch(a.err, code);
+        abort_flag = 1;
+    };
+
+    if (warp == 0) {
+        // ---------------- producer: bulk copies of the column segments ----------------
+        if (lane == 0) {
+            int j = 0;
+            for (; j < njobs && !abort_flag; j++) {
+                const int s = j % AY_NSTG, kc = j % a.nch;
+                if (j >= AY_NSTG) {
+                    if (!mbar_wait(&stg_free[s], ((j / AY_NSTG) - 1) & 1)) {
+                        fail(11);
+                        break;
+                    }
+                    // the workers read this slot through the generic proxy; the copies write it
+                    // through the async proxy
+                    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                }
+                const long n0 = (long)job_tile(j) * TM;
+                const long rows = min((long)TM, a.nrows - n0);
+                const int c0 = kc * AY_COLS, nc = min(AY_COLS, a.nA - c0);
+                mbar_expect_tx(&stg_full[s], (unsigned)(nc * rows * 8));
+                for (int c = 0; c < nc; c++) {
+                    const float2 *col = a.A + (a.aoff ? a.aoff[c0 + c] : (long)(c0 + c) * a.acol);
+                    bulk_g2s(stg + s * stg_bytes + c * TM * 8, col + n0, (unsigned)(rows * 8), &stg_full[s]);
+                }
+            }
+            n_issued = j;
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            const uint32_t idesc = idesc_tf32(TM, N);
+            for (int j = 0; j < njobs && !abort_flag; j++) {
+                const int o = j % AY_NOP, kc = j % a.nch, ti = j / a.nch;
+                if (!mbar_wait(&op_ready[o], (j / AY_NOP) & 1)) {
+                    fail(12);
+                    break;
+                }
+                if (kc == 0 && ti >= 2 && !mbar_wait(&acc_empty[ti & 1], ((ti >> 1) - 1) & 1)) {
+                    fail(13);
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                unsigned char *Ahi = ops + o * op_bytes, *Alo = Ahi + a_bytes;
+                unsigned char *Bhi = Ahi + 2 * a_bytes, *Blo = Bhi + b_bytes;
+                const uint32_t d = tmem + (uint32_t)((ti & 1) * ACOLS);
+                const uint64_t ah0 = sdesc(sa(Ahi)), al0 = sdesc(sa(Alo)), bh0 = sdesc(sa(Bhi)), bl0 = sdesc(sa(Blo));
+#pragma unroll
+                for (int ks = 0; ks < KT / 8; ks++) {
+                    const uint64_t o = 2 * ks;  // 32 bytes along the swizzled row
+                    mma_tf32(d, ah0 + o, bh0 + o, idesc, (kc > 0 || ks > 0) ? 1 : 0);
+                    mma_tf32(d, ah0 + o, bl0 + o, idesc, 1);
+                    mma_tf32(d, al0 + o, bh0 + o, idesc, 1);
+                }
+                mma_commit(&op_free[o]);
+                if (kc == a.nch - 1) mma_commit(&acc_full[ti & 1]);
+            }
+            mma_commit(&done);
+        }
+    } else {
+        // ---------------- workers ----------------
+        const int wt = t - 64, quarter = warp & 3, half = (warp - 2) >> 2;
+        constexpr int NB = N * KT / (32 * WORKERS);  // Yt elements per worker thread
+        auto load_y = [&](int j, double2 *yv) {
+#pragma unroll
+            for (int m = 0; m < NB; m++) {
+                const int i = wt + m * 32 * WORKERS, r = i / KT, al = (i % KT) >> 1, c = r >> 1;
+                const int col = (j % a.nch) * AY_COLS + al;
+                yv[m] = make_double2(0.0, 0.0);
+                if (j < njobs && c < a.k && col < a.nA)
+                    yv[m] = reinterpret_cast<const double2 *>(a.Y)[(long)col * a.k + c];
+            }
+        };
+        // outputs of tile ti (rows n0 ..), from accumulator ti & 1; warp-uniform
+        auto epilogue = [&](int ti) {
+            const bool ok = __all_sync(0xffffffffu, mbar_wait(&acc_full[ti & 1], (ti >> 1) & 1));
+            if (!ok) {
+                fail(14);
+                return false;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            constexpr int HC = N / 2;
+            uint32_t v[HC];
+            const uint32_t addr = tmem + (uint32_t)((ti & 1) * ACOLS) + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * HC);
+            if constexpr (HC == 8) {
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+                             : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                               "=r"(v[7])
+                             : "r"(addr)
+                             : "memory");
+            } else {
+#pragma unroll
+                for (int c0 = 0; c0 < HC; c0 += 16)
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+                        "%15}, [%16];\n"
+                        : "=r"(v[c0 + 0]), "=r"(v[c0 + 1]), "=r"(v[c0 + 2]), "=r"(v[c0 + 3]), "=r"(v[c0 + 4]),
+                          "=r"(v[c0 + 5]), "=r"(v[c0 + 6]), "=r"(v[c0 + 7]), "=r"(v[c0 + 8]), "=r"(v[c0 + 9]),
+                          "=r"(v[c0 + 10]), "=r"(v[c0 + 11]), "=r"(v[c0 + 12]), "=r"(v[c0 + 13]), "=r"(v[c0 + 14]),
+                          "=r"(v[c0 + 15])
+                        : "r"(addr + c0)
+                        : "memory");
+            }
+            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[ti & 1]);
+            const long n = (long)((int)blockIdx.x + ti * (int)gridDim.x) * TM + quarter * 32 + lane;
+            if (n < a.nrows) {
+#pragma unroll
+                for (int q = 0; q < HC / 2; q++) {
+                    const int c = half * (HC / 2) + q;
+                    if (c < a.k) {
+                        float2 *op = a.ooff ? a.Out + a.ooff[c] + n
+                                            : a.Out + ((n >> 1) * a.oki + c % a.oki) * 2 + (n & 1) + (long)(c / a.oki) * a.ocol;
+                        float2 r = make_float2(__uint_as_float(v[2 * q]), __uint_as_float(v[2 * q + 1]));
+                        if (a.beta != 0.f) {
+                            const float2 old = *op;
+                            r.x += a.beta * old.x;
+                            r.y += a.beta * old.y;
+                        }
+                        *op = r;
+                    }
+                }
+            }
+            return true;
+        };
+        double2 ycur[NB], ynext[NB];
+        load_y(0, ycur);
+        int j = 0, pending = -1;  // tile whose outputs are still to be written
+        bool ok = true;
+        for (; j < njobs && ok && !abort_flag; j++) {
+            const int s = j % AY_NSTG, o = j % AY_NOP, kc = j % a.nch;
+            const long n0 = (long)job_tile(j) * TM;
+            const long rows = min((long)TM, a.nrows - n0);
+            const int nc = min(AY_COLS, a.nA - kc * AY_COLS);
+            load_y(j + 1, ynext);
+            if (!__all_sync(0xffffffffu, mbar_wait(&stg_full[s], (j / AY_NSTG) & 1))) {
+                fail(15);
+                break;
+            }
+            if (j >= AY_NOP && !__all_sync(0xffffffffu, mbar_wait(&op_free[o], ((j / AY_NOP) - 1) & 1))) {
+                fail(16);
+                break;
+            }
+            unsigned char *Ahi = ops + o * op_bytes, *Alo = Ahi + a_bytes;
+            unsigned char *Bhi = Ahi + 2 * a_bytes, *Blo = Bhi + b_bytes;
+            {
+                // transpose + split: worker thread (row n, half h) takes columns 8h .. 8h + 7 of its row
+                const int n = wt & (TM - 1), h = wt >> 7;
+                const float2 *sg = reinterpret_cast<const float2 *>(stg + s * stg_bytes);
+                float v[16];
+#pragma unroll
+                for (int q = 0; q < 8; q++) {
+                    const int c = 8 * h + q;
+                    float2 x = make_float2(0.f, 0.f);
+                    if (c < nc && n < rows) x = sg[c * TM + n];
+                    v[2 * q] = x.x;
+                    v[2 * q + 1] = x.y;
+                }
+#pragma unroll
+                for (int q4 = 0; q4 < 4; q4++) {  // K positions 16h + 4 q4 .. + 3
+                    float hv[4], lv[4];
+#pragma unroll
+                    for (int e = 0; e < 4; e++) {
+                        hv[e] = hi_tf32(v[4 * q4 + e]);
+                        lv[e] = v[4 * q4 + e] - hv[e];
+                    }
+                    const uint32_t off = sw128(n, 16 * h + 4 * q4);
+                    *reinterpret_cast<float4 *>(Ahi + off) = make_float4(hv[0], hv[1], hv[2], hv[3]);
+                    *reinterpret_cast<float4 *>(Alo + off) = make_float4(lv[0], lv[1], lv[2], lv[3]);
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&stg_free[s]);  // the staging slot has been read
+            // B = Yt for this chunk: row r = 2c + e (output c, re/im), K position 2 al + e'
+#pragma unroll
+            for (int m = 0; m < NB; m++) {
+                const int i = wt + m * 32 * WORKERS, r = i / KT, kk = i % KT, ep = kk & 1, e = r & 1;
+                const double yr = ycur[m].x, yi = ycur[m].y;
+                const float y = (float)(e == 0 ? (ep == 0 ? yr : -yi) : (ep == 0 ? yi : yr));
+                const float yh = hi_tf32(y);
+                *reinterpret_cast<float *>(Bhi + sw128(r, kk)) = yh;
+                *reinterpret_cast<float *>(Blo + sw128(r, kk)) = y - yh;
+            }
+#pragma unroll
+            for (int m = 0; m < NB; m++) ycur[m] = ynext[m];
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&op_ready[o]);
+            // the previous tile's outputs, one chunk after its last MMA was issued
+            if (pending >= 0) {
+                ok = epilogue(pending);
+                pending = -1;
+            }
+            if (kc == a.nch - 1) pending = j / a.nch;
+        }
+        if (wt == 0) n_consumed = j;
+        if (ok && pending >= 0 && !abort_flag) epilogue(pending);
+    }
+    __syncthreads();
+    if (t == 0)
+        for (int j = n_consumed; j < n_issued; j++) mbar_wait(&stg_full[j % AY_NSTG], (j / AY_NSTG) & 1);
+    if (!mbar_wait(&done, 0)) atomicExch(a.err, 17);
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(2 * ACOLS) : "memory");
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
@@ -450,19 +802,67 @@ cudaError_t launch_tc_ahb(const ColSet &A, const ColSet &B, long nrows, double *
     int grid = 0;
     tc_grid(a.ktiles, &a.chunk, &grid);
     const size_t stage = 2 * MT * (size_t)(TM * KT * 4) + 2 * (size_t)((N + 7) / 8) * 1024;
-    const size_t smem = STAGES * stage + 1024;
+    const size_t smem = (MT == 1 ? 5 : 3) * stage + 1024;  // stages of the TMA ring (k_tc_ahb's NS)
     auto go = [&](auto kern) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        kern<<<grid, THREADS, smem, s>>>(map, a);
+        kern<<<grid, TC_THREADS, smem, s>>>(map, a);
     };
-    if (MT == 1 && N == 16) go(k_tc_ahb<1, 16>);
-    else if (MT == 1) go(k_tc_ahb<1, 32>);
-    else if (N == 16) go(k_tc_ahb<2, 16>);
-    else go(k_tc_ahb<2, 32>);
+    if (MT == 1 && N == 16) go(k_tc_ahb<1, 16, 5>);
+    else if (MT == 1) go(k_tc_ahb<1, 32, 5>);
+    else if (N == 16) go(k_tc_ahb<2, 16, 3>);
+    else go(k_tc_ahb<2, 32, 3>);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int n = l * k;
     k_tc_reduce<<<(n + 127) / 128, 128, 0, s>>>(partials, grid, MT, N, l, k, C);
+    return cudaGetLastError();
+}
+
+bool tc_ay_ok(const ColSet &A, const ColSet &Out) {
+    if (A.f64 || Out.f64 || A.ki != 1) return false;
+    if (A.ncols < 1 || A.ncols > 512 || Out.ncols < 1 || Out.ncols > 32) return false;
+    if (((uintptr_t)A.base & 15) != 0 || ((uintptr_t)Out.base & 7) != 0) return false;
+    if (!A.col_off && (A.col_stride & 1)) return false;  // 16-byte aligned column segments
+    if (Out.col_off) return Out.ki == 1;
+    if (Out.ki == 1) return true;
+    return Out.ki == Out.ncols && Out.col_stride == 0;
+}
+
+// Out = beta Out + A Y (FP32 column sets, Y FP64 nA x nOut complex row-major, device).
+// A's column offsets (col_off) must be even, as every window slot offset is.
+cudaError_t launch_tc_ay(const ColSet &A, const double *Y, const ColSet &Out, double beta, long nrows, int *err,
+                         cudaStream_t s) {
+    if (!tc_ay_ok(A, Out) || (nrows & 1)) return cudaErrorInvalidValue;
+    ProfScope prof("tc_gemm_ay", (double)nrows * (A.ncols + Out.ncols * (beta != 0.0 ? 2 : 1)) * 8.0, s);
+    AyArgs a;
+    a.A = static_cast<const float2 *>(A.base);
+    a.aoff = A.col_off;
+    a.acol = A.col_stride;
+    a.nA = A.ncols;
+    a.Y = Y;
+    a.Out = static_cast<float2 *>(Out.base);
+    a.oki = Out.ki;
+    a.ocol = Out.col_stride;
+    a.ooff = Out.col_off;
+    a.k = Out.ncols;
+    a.beta = (float)beta;
+    a.nrows = nrows;
+    a.mtiles = (int)((nrows + TM - 1) / TM);
+    a.nch = (A.ncols + AY_COLS - 1) / AY_COLS;
+    a.err = err;
+    const int N = 2 * Out.ncols <= 16 ? 16 : (2 * Out.ncols <= 32 ? 32 : 64);
+    int grid = device_sm_count();
+    if (grid > a.mtiles) grid = a.mtiles;
+    const int nstg = N <= 32 ? 6 : 5;  // AyStages<N>
+    const size_t smem =
+        nstg * (size_t)(AY_COLS * TM * 8) + AY_NOP * (2 * (size_t)(TM * KT * 4) + 2 * (size_t)(N / 8) * 1024) + 1024;
+    auto go = [&](auto kern) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        kern<<<grid, AY_THREADS, smem, s>>>(a);
+    };
+    if (N == 16) go(k_tc_ay<16>);
+    else if (N == 32) go(k_tc_ay<32>);
+    else go(k_tc_ay<64>);
     return cudaGetLastError();
 }
 

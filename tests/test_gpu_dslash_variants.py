@@ -2,7 +2,8 @@
 
 The library picks the fastest of eight variants (staged or direct loads, one or two
 RHS per thread, register budgets, L1 prefetch) per lattice and k; EIG_DSLASH_VARIANT forces one
-for the whole process, so each variant runs in a subprocess of its own.  Each one
+for the whole process (EIG_DSLASH_LINKS the FP32 link format: 12 or 18 reals), so
+each variant runs in a subprocess of its own.  Each one
 must meet the FP32 (1e-6) and FP16 (5e-3) matvec bars of test_gpu_dslash.py for M,
 M^H and A, on a lattice with a ragged last block and on 8^4, with k = 1 and 4, and
 with the CG epilogue (an init-CG solve reaching 1e-8 in mixed precision).
@@ -48,13 +49,15 @@ print("variant ok")
 """
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6, 7])
-def test_variant_parity(variant):
+@pytest.mark.parametrize("variant,links", [(v, None) for v in range(8)] + [(v, "18") for v in (2, 4, 6)])
+def test_variant_parity(variant, links):
     import torch
 
     if not torch.cuda.is_available():
         pytest.skip("no GPU")
     env = dict(os.environ, EIG_DSLASH_VARIANT=str(variant))
+    if links:
+        env["EIG_DSLASH_LINKS"] = links  # FP32 ops: 12- or 18-real links
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     p = subprocess.run([sys.executable, "-c", CHILD], env=env, cwd=root, capture_output=True, text=True,
                        timeout=600)

@@ -1,8 +1,8 @@
 """Tensor-core (tcgen05) U^H r of the Eq. 1 deflation against the CUDA-core kernel
 and the oracle.
 
-EIG_GEMM_TC=1 routes the U^H r contraction of eig_basis_deflate through the
-tcgen05 kernel (TF32 hi/lo split, three products per K step, TMEM accumulators
+The FP32 contractions run on the tensor cores unless EIG_GEMM_TC=0 (then on CUDA
+cores); U^H r of eig_basis_deflate goes through the tcgen05 kernel (TF32 hi/lo split, three products per K step, TMEM accumulators
 drained every two K tiles into double-float sums, FP64 sum over CTAs).  On 8^4
 each CTA runs 21 K tiles, so the pipeline wraps and several drains happen.  Its result agrees with FP32 arithmetic:
 the deflated guess x0 = U H^{-1} U^H b matches the oracle's FP64 evaluation on
@@ -161,3 +161,44 @@ def test_tc_accuracy_at_scale():
         os.environ.pop("EIG_GEMM_TC", None)
         basis.close()
         op.close()
+
+
+def test_eigcg_restart_on_tensor_cores():
+    """eigCG(10, 40) on 8^4: the window restart V <- V QZ (in place, tensor cores) and
+    w^H V_new give the same run as the CUDA-core restart kernel: iteration counts within
+    2, the lowest 5 pending Ritz values within 1e-5 relative (FP32 window arithmetic) and
+    all 10 within 1e-4, both solutions at tol."""
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_0707_0131_gb300 import api
+
+    dims = fx.LATTICES["8^4"]
+    m_q = MASSES["8^4"]["1e+04"]["m_q"]
+    gauge = fx.make_gauge(dims, fx.GAUGE_SEEDS["8^4"])
+    W = oracle.Wilson(dims, m_q, gauge)
+    b = fx.make_rhs(dims, 5500)[0].reshape(-1)
+    runs = {}
+    try:
+        for tc in (True, False):
+            os.environ["EIG_GEMM_TC"] = "1" if tc else "0"
+            op = api.Op(gauge, dims, m_q, prec=32)
+            basis = api.Basis(op, 16)
+            x = np.zeros_like(b)
+            st = op.eigcg_solve(b, x, nev=10, m=40, tol=1e-8, basis=basis)
+            basis.grow()
+            ev, _ = basis.ritz(residuals=False)
+            runs[tc] = (st, np.sort(ev), x)
+            assert st["restarts"] >= 3
+            assert np.linalg.norm(b - W.A(x)) / np.linalg.norm(b) <= 1e-8
+            basis.close()
+            op.close()
+    finally:
+        os.environ.pop("EIG_GEMM_TC", None)
+    (s1, e1, _), (s0, e0, _) = runs[True], runs[False]
+    assert abs(s1["iters"] - s0["iters"]) <= 2, (s1["iters"], s0["iters"])
+    # both restarts run in FP32 window arithmetic: the Ritz values agree to the FP32
+    # rounding of A (about eps_32 ||A|| absolute; ~1e-8 here against lambda ~ 6e-3)
+    rel = np.abs(e1 - e0) / e0
+    assert np.max(rel[:5]) < 1e-5 and np.max(rel) < 1e-4, (e1, e0)
