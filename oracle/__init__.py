@@ -7,9 +7,10 @@ multiple right hand side linear systems ..."):
   wilson.c / wilson.py   M = m_q I - D (Sec. 1), M^H = gamma5 M gamma5, A = M^H M
   wilson_eo.py           odd-even (Schur complement) form: M_hat on odd sites, its normal
                          equations, preparation of b and reconstruction of x (Sec. 5)
-  solvers.py             CG and eigCG (Fig. 1), full-history Lanczos (Eq. 4, Sec. 3.1),
-                         init-CG (Eq. 1) with its restart (Sec. 5.3),
-                         Incremental eigCG and Rayleigh-Ritz on U (Sec. 4 box, Sec. 5.2)
+  solvers.py             CG and eigCG (Fig. 1, with an optional preconditioner P, Sec. 3),
+                         full-history Lanczos (Eq. 4, Sec. 3.1), init-CG (Eq. 1) with its
+                         restart (Sec. 5.3), Incremental eigCG and Rayleigh-Ritz on U
+                         (Sec. 4 box, Sec. 5.2), the spectral preconditioner from U (Sec. 2)
 
 Only tests/, __graft_entry__.smoke() and the CPU-baseline leg of bench.py may
 import this package.  It shares no code with the CUDA library; the two meet only
@@ -18,7 +19,9 @@ through the seeded input generators (the package's fixtures module).
 Parity pins (tests/test_oracle_*.py): free-field spectrum in closed form, plane
 waves, gamma5-Hermiticity, Hermiticity and positivity of A, gauge covariance,
 dense solves and eigensolves on 4^4, CG/eigCG bit-identity, T = V^H A V, Galerkin
-condition of Eq. 1, the Schur identity against the full operator and the free-field
+condition of Eq. 1, PCG against CG on the split system, the spectrum of the spectrally
+preconditioned operator in closed form, P-orthonormality of the preconditioned eigCG
+window, the Schur identity against the full operator and the free-field
 spectrum of the odd-site normal equations in closed form.  Parity of the eigen part at the paper's own scale (its
 figures, on ensembles that are not available) is unpinned.
 """

@@ -56,8 +56,9 @@ def _orth(X: np.ndarray, m_scale: int) -> np.ndarray:
 # ----------------------------------------------------------------------------------------
 # CG, Fig. 1 left box, with P = I (z = r)
 # ----------------------------------------------------------------------------------------
-def cg(A, b, x0=None, tol=1e-10, max_iter=100000):
-    """Conjugate Gradient of Fig. 1 (left box) with P = I.
+def cg(A, b, x0=None, tol=1e-10, max_iter=100000, Pinv=None):
+    """Conjugate Gradient of Fig. 1 (left box); Pinv (a callable r -> P^{-1} r for an
+    HPD preconditioner P) applies step 3, P = I when None.
 
     Returns dict(x, iters, res (recursive ||r||/||b|| per iteration, entry 0 =
     start), alphas, betas (betas[j-1] = beta_j, beta_1 = 0), true_rel_res)."""
@@ -75,8 +76,8 @@ def cg(A, b, x0=None, tol=1e-10, max_iter=100000):
         if np.sqrt(rr) <= tol * bnorm or j >= max_iter:  # step 1
             break
         j += 1  # step 2
-        z = r  # step 3 (P = I)
-        rho_prev, rho = rho, rr  # step 4: rho = r^H z
+        z = r if Pinv is None else np.asarray(Pinv(r), dtype=np.complex128)  # step 3
+        rho_prev, rho = rho, (rr if Pinv is None else np.vdot(r, z).real)  # step 4: rho = r^H z
         if j == 1:  # steps 5-6
             p = z.copy()
             beta = 0.0
@@ -110,8 +111,9 @@ def lanczos_tridiagonal(alphas, betas, j: int) -> np.ndarray:
 # ----------------------------------------------------------------------------------------
 # eigCG(nev, m), Fig. 1 right box
 # ----------------------------------------------------------------------------------------
-def eigcg(A, b, x0=None, nev=8, m=24, tol=1e-10, max_iter=100000, on_restart=None):
-    """CG of Fig. 1 with the eigCG(nev, m) additions of its right box.
+def eigcg(A, b, x0=None, nev=8, m=24, tol=1e-10, max_iter=100000, on_restart=None, Pinv=None):
+    """CG of Fig. 1 with the eigCG(nev, m) additions of its right box; Pinv as in cg()
+    (the window then holds z / sqrt(r^H z), P-orthonormal, and T = V^H A V, Sec. 3).
 
     on_restart(j, V, T, ritz) -- optional observer called after each restart with
     the restarted window V (N x i), its projection T (i x i) and the Ritz values.
@@ -139,8 +141,8 @@ def eigcg(A, b, x0=None, nev=8, m=24, tol=1e-10, max_iter=100000, on_restart=Non
         if np.sqrt(rr) <= tol * bnorm or j >= max_iter:  # step 1
             break
         j += 1  # step 2
-        z = r  # step 3 (P = I)
-        rho_prev, rho = rho, rr  # step 4
+        z = r if Pinv is None else np.asarray(Pinv(r), dtype=np.complex128)  # step 3
+        rho_prev, rho = rho, (rr if Pinv is None else np.vdot(r, z).real)  # step 4
         if j == 1:  # steps 5-6
             p = z.copy()
             beta = 0.0
@@ -339,3 +341,24 @@ def basis_ritz(A, U, H):
     X = U @ S
     res = np.array([_norm(A(X[:, c]) - theta[c] * X[:, c]) for c in range(X.shape[1])])
     return theta, res, X
+
+
+# ----------------------------------------------------------------------------------------
+# Spectral preconditioner from the deflation basis (Sec. 2, "using U as a spectral
+# preconditioner"; Sec. 4 and 5.2 suggest it for eigCG near the critical mass)
+# ----------------------------------------------------------------------------------------
+def spectral_preconditioner(U, H, shift):
+    """P^{-1} = (I - U U^H) + shift * U H^{-1} U^H for an orthonormal U with H = U^H A U.
+
+    HPD for shift > 0.  When U spans an invariant subspace of A, P^{-1} A keeps the
+    eigenpairs of A outside span(U) and maps the ones inside to the value shift, so the
+    lowest part of the spectrum, the part U has captured, stops slowing CG down.
+    Returns the callable r -> P^{-1} r."""
+    U = np.asarray(U, dtype=np.complex128)
+    H = np.asarray(H, dtype=np.complex128)
+
+    def apply(r):
+        c = np.conj(U.T) @ r
+        return r - U @ c + shift * (U @ np.linalg.solve(H, c))
+
+    return apply
