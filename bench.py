@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--serve-basis", type=int, default=40)
     ap.add_argument("--budget-gb", type=float, default=150.0)
     ap.add_argument("--prec", type=int, default=32)
+    ap.add_argument("--reliable-delta", type=float, default=0.1,
+                    help="residual replacement when ||r|| fell by this factor since the last one")
     ap.add_argument("--links", type=int, default=12, choices=[12, 18],
                     help="FP32 link storage: 12 reals (third row rebuilt) or all 18")
     ap.add_argument("--which", type=int, default=2, help="dslash mode: 0 M, 1 M^H, 2 A")
@@ -335,7 +337,7 @@ def main():
     m_q, mass_src = mass_for(a.lattice, a.kappa)
     gauge = fx.make_gauge(dims, fx.GAUGE_SEEDS[a.lattice])
     k = a.k
-    op = Op(gauge, dims, m_q, prec=32, max_rhs=k, compress12=a.links == 12)
+    op = Op(gauge, dims, m_q, prec=32, max_rhs=k, compress12=a.links == 12, reliable_delta=a.reliable_delta)
     basis = Basis(op, a.basis + a.nev)
     nrhs_id = [0]
 
@@ -413,8 +415,12 @@ def main():
     else:
         peak, peak_src = 6800.0, "fallback"
     achieved = (kp["bytes"] / kp["launches"]) / (kp["ms"] / kp["launches"] / 1e3) / 1e9
+    # the stencil variant and link form the autotuner chose for that kernel's batch width
+    kk = int(kern.rsplit("_k", 1)[1]) if "_k" in kern else 1
+    kvar, klinks = op.stencil_choice(kk)
     # DRAM traffic from an ncu capture of this kernel (configs/traffic_from_ncu.py): the
-    # measured DRAM / algorithmic byte ratio, valid while the stencil sources match
+    # measured DRAM / algorithmic byte ratio, valid while the stencil sources, the variant
+    # and the link form match the capture's
     traffic = None
     tfile = os.path.join(ROOT, "configs", "traffic.json")
     if os.path.exists(tfile):
@@ -422,10 +428,12 @@ def main():
         h = hashlib.sha1()
         for f in ("dslash32.cuh", "dslash32.cu", "dslash32d_rb1.cu", "dslash32d_rb2.cu"):
             h.update(open(os.path.join(ROOT, "paper_0707_0131_gb300", "csrc", f), "rb").read())
-        if tj.get("stencil_sha1") == h.hexdigest():
+        if (tj.get("stencil_sha1") == h.hexdigest() and tj.get("variant") == kvar
+                and tj.get("link_reals") == klinks):
             traffic = tj["dram_over_algorithmic"] * kp["bytes"] / kp["launches"]
     roofline = {"bound": "hbm", "kernel": kern, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_src, "traffic": traffic,
+                "variant": kvar, "link_reals": klinks,
                 "algorithmic_bytes_per_launch": kp["bytes"] / kp["launches"],
                 "avg_launch_ms": kp["ms"] / kp["launches"], "launches": kp["launches"]}
     kernels = {n: {"launches": v["launches"], "ms": round(v["ms"], 3),
@@ -482,7 +490,7 @@ def main():
                                       f"per step 1 eigCG({a.nev},{a.m}) + grow + k={k} batched init-CG, "
                                       f"basis {l0} FP32 vectors, tol {a.tol}, restart {a.restart_tol}",
                           "lattice": a.lattice, "k": k, "basis": l0, "storage": "fp32 spinors, fp32 links (12- and 18-real resident, chosen per k by the autotuner), "
-                          "double-float residual replacements, fp64 final residual", "l2": "inputs larger than L2 (each field >= 85 MB)",
+                          f"double-float residual replacements (delta {a.reliable_delta}), fp64 final residual", "l2": "inputs larger than L2 (each field >= 85 MB)",
                           "parallelism": f"replicas{world}"},
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                "clocks": clk, "plain_fp64_eigcg": plain,

@@ -6,8 +6,11 @@ output moved once) is stored together with a hash of the stencil sources; bench.
 reports traffic = ratio x algorithmic bytes per launch while the sources still match,
 and null otherwise.
 
-usage: python configs/traffic_from_ncu.py CSV --name dslash_cg_f32 --sites V --k K --links 12|18
-       [--note "how the capture was made"]
+usage: python configs/traffic_from_ncu.py CSV --name dslash_cg_f32_k16 --sites V --k K --links 12|18
+       --variant N [--note "how the capture was made"]
+
+The name is the profile name of the launches (dslash_cg_f32 for one RHS, dslash_cg_f32_kK
+for K), the variant the stencil variant the capture ran (EIG_DSLASH_VARIANT=N).
 """
 import argparse
 import csv
@@ -34,10 +37,11 @@ def cg_algorithmic_bytes(sites: int, k: int, links: int) -> float:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("csv")
-    ap.add_argument("--name", default="dslash_cg_f32")
+    ap.add_argument("--name", default="dslash_cg_f32_k16")
     ap.add_argument("--sites", type=int, required=True)
     ap.add_argument("--k", type=int, required=True)
     ap.add_argument("--links", type=int, default=12)
+    ap.add_argument("--variant", type=int, required=True)
     ap.add_argument("--note", default="")
     a = ap.parse_args()
     per = {}
@@ -51,14 +55,19 @@ def main():
         if r[i_m] in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
             per.setdefault(r[i_id], 0.0)
             per[r[i_id]] += float(r[i_v].replace(",", "")) * scale.get(r[unit_i], 1)
-    launches = list(per.values())
     alg = cg_algorithmic_bytes(a.sites, a.k, a.links)
+    # the same kernel may also run single-RHS products (the eigCG solves): keep the
+    # launches whose traffic is that of a k-RHS product
+    launches = [b for b in per.values() if b >= 0.5 * alg]
+    if not launches:
+        raise SystemExit("no captured launch moves the bytes of a %d-RHS product" % a.k)
     ratio = sum(launches) / len(launches) / alg
     out_path = os.path.join(ROOT, "configs", "traffic.json")
     data = json.load(open(out_path)) if os.path.exists(out_path) else {}
     data[a.name] = {"dram_over_algorithmic": ratio, "launches_captured": len(launches),
                     "dram_bytes_per_launch": sum(launches) / len(launches), "algorithmic_bytes_per_launch": alg,
-                    "stencil_sha1": stencil_sha1(), "capture": a.note}
+                    "stencil_sha1": stencil_sha1(), "variant": a.variant, "link_reals": a.links,
+                    "capture": a.note}
     json.dump(data, open(out_path, "w"), indent=1)
     print(json.dumps(data[a.name], indent=1))
 

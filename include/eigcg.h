@@ -51,7 +51,8 @@ typedef enum {
     EIG_ERR_BUDGET = -3,    /* request exceeds the handle's capacity                */
     EIG_ERR_CUDA = -4,      /* CUDA runtime error (message in eig_last_error)       */
     EIG_ERR_BREAKDOWN = -5, /* CG breakdown: p^H A p <= 0, rho <= 0, NaN or Inf     */
-    EIG_ERR_TIMEOUT = -6    /* a bounded device wait gave up                        */
+    EIG_ERR_TIMEOUT = -6,   /* a bounded device wait gave up                        */
+    EIG_ERR_IO = -7         /* a basis file could not be opened, read or written    */
 } eig_status;
 
 /* Storage precision codes for spinor_prec. */
@@ -70,6 +71,14 @@ typedef struct {
     int max_rhs;            /* largest k of one batched call (1..16); sizes buffers      */
     double reliable_delta;  /* mixed precision: FP64 residual update when ||r|| falls by
                                this factor since the last one (0 -> 0.1)                  */
+    int even_odd;           /* 1: the odd-even (Schur complement) form, Sec. 5: the op's
+                               matrix is A_hat = M_hat^H M_hat on the odd sites, with
+                               M_hat = d - (1/d) H_oe H_eo, d = 4 + m_q, H = M - d the
+                               hopping part; every extent must be even.  Solves then take
+                               the full-lattice b and x of the Dirac equation M x = b (see
+                               eig_eigcg_solve); the vectors of eig_op_apply,
+                               eig_basis_deflate and eig_basis_vector are odd-site vectors
+                               ([rhs][V/2][4][3], odd site s at s/2).  0: the full lattice. */
 } eig_op_opts;
 
 typedef struct {
@@ -97,6 +106,16 @@ eig_status eig_op_destroy(eig_op op);
  * This is the dslash of the CG matrix-vector product (Fig. 1 step 11). */
 eig_status eig_op_apply(eig_op op, int which, const double *in, double *out, int k, void *stream);
 
+/* The stencil launch the autotuner chose for k-RHS products of an FP32/FP16 op (the
+ * matrix-vector product of Fig. 1 step 11, timed per shape on the first solve):
+ * *variant 0..7 (0, 1: shared-memory staged loads of 1 or 2 RHS per thread; 2, 3, 7:
+ * direct loads of 1 RHS per thread at 4 or 5 resident blocks per SM, 7 with L1
+ * prefetch; 4, 5, 6: direct loads of 2 RHS per thread, 6 with L1 prefetch) and
+ * *link_reals 12 or 18 (the resident FP32 link form used).  Both are -1 and 0 for FP64
+ * ops or before the first solve with k RHS.  Odd-even ops report the half stencil.
+ * Errors: EIG_ERR_ARG (null pointer, k not a power of two <= max_rhs). */
+eig_status eig_op_stencil_choice(eig_op op, int k, int *variant, int *link_reals);
+
 /* Deflation basis U (N x l, l <= max_vecs) with H = U^H A U in FP64 (Sec. 4 box),
  * stored on the device in the op's window precision (FP64 for F64 ops, else
  * FP32), plus a pending block of eigCG Ritz vectors.  Bound to one op. */
@@ -113,9 +132,29 @@ eig_status eig_basis_truncate(eig_basis basis, int l);
  * ||r|| <= tol ||b||, then checks the FP64 true residual (mixed precision:
  * reliable updates continue until it meets tol).  On return the nev lowest Ritz
  * pairs of the final window are pending in the basis (if given).
- * Requires 1 <= nev, 2*nev < m <= 128.  stats may be NULL. */
+ * Requires 1 <= nev, 2*nev < m <= 128.  stats may be NULL.
+ * Odd-even ops: b and x (initial guess in, solution out) are full-lattice vectors of
+ * M x = b; CG runs on A_hat x_o = M_hat^H b_hat, b_hat = b_o - (1/d) H_oe b_e (Sec. 5,
+ * "odd-even preconditioned normal equations"), x_e = (b_e - H_eo x_o) / d is
+ * reconstructed, and tol and true_rel_res refer to the odd-site normal equations. */
 eig_status eig_eigcg_solve(eig_op op, eig_basis basis, const double *b, double *x, int nev, int m, double tol,
                            int max_iter, eig_stats *stats, void *stream);
+
+/* Spectrally preconditioned eigCG (Sec. 2 "using U as a spectral preconditioner";
+ * Sec. 5.2 proposes it for better interior eigenvectors near the critical mass): as
+ * eig_eigcg_solve, with Fig. 1's preconditioner P^{-1} = (I - U_p U_p^H) +
+ * sp_shift U_p H_p^{-1} U_p^H built from the first sp_vecs basis vectors U_p and the
+ * leading block H_p of H (step 3: z = P^{-1} r, rho = r^H z; the window holds
+ * z / sqrt(rho)).  For an invariant U_p, P^{-1} A keeps A's other eigenpairs and moves
+ * those in span(U_p) to sp_shift, so sp_shift should lie above the eigenvalues wanted
+ * next (an upper estimate of A's spectrum, e.g. (8 + m_q)^2 for the full lattice).  The
+ * pending Ritz vectors are those of P^{-1} A, to be added by eig_basis_grow.  Each
+ * iteration adds U_p^H r and U_p y (two passes over U_p) to the CG work.
+ * Requires a non-empty basis, 1 <= sp_vecs <= its size, sp_shift > 0, an FP64 or FP32
+ * op.  Errors: as eig_eigcg_solve; EIG_ERR_BREAKDOWN if H_p is not positive definite
+ * or r^H z <= 0. */
+eig_status eig_eigcg_solve_sp(eig_op op, eig_basis basis, const double *b, double *x, int nev, int m, double tol,
+                              int max_iter, int sp_vecs, double sp_shift, eig_stats *stats, void *stream);
 
 /* Sec. 4 box, last three lines: orthonormalises the pending Ritz vectors against U
  * (classical Gram-Schmidt twice, FP64 accumulation), W = A V-bar in FP64, extends H
@@ -142,8 +181,29 @@ eig_status eig_basis_ritz(eig_basis basis, double *evals, double *resnorms, int 
 
 /* Copies basis vector j (0 <= j < l) to out (natural layout, host or device). */
 eig_status eig_basis_vector(eig_basis basis, int j, double *out, void *stream);
+/* Ritz values of the pending block the last eigCG solve left (ascending, *n of them,
+ * at most nev; evals may be NULL to query *n): the eigenvalues of Fig. 1's final
+ * window that eig_basis_grow will add. */
+eig_status eig_basis_pending(eig_basis basis, double *evals, int *n);
 /* Copies H (l x l, FP64 complex, row-major, host) to out. */
 eig_status eig_basis_h(eig_basis basis, double *out);
+
+/* Saves the deflation basis U and H = U^H A U (Sec. 4 box) to a file, so that later
+ * jobs with the same operator start from it instead of rebuilding it with Incremental
+ * eigCG (the paper notes the vectors can be stored for reuse).  Layout: a 64-byte
+ * header (magic "EIGBASIS", version 1, the four lattice extents, even_odd, bytes per
+ * real of the stored vectors, l, complex entries per vector, m_q, a fingerprint of the
+ * FP64 links), H as l x l complex FP64 row-major, then the l vectors in natural layout
+ * in the basis precision (FP32 for FP32/FP16 ops, FP64 otherwise), little-endian.  The
+ * pending Ritz block is not saved.  Errors: EIG_ERR_ARG, EIG_ERR_IO, EIG_ERR_CUDA. */
+eig_status eig_basis_save(eig_basis basis, const char *path, void *stream);
+/* Replaces the basis with one saved by eig_basis_save for an operator with the same
+ * lattice, odd-even form, quark mass and links (else EIG_ERR_ARG); the vectors are
+ * converted to this basis's precision.  EIG_ERR_BUDGET if the file holds more than
+ * max_vecs vectors (basis unchanged); EIG_ERR_IO for an unreadable or short file
+ * (basis left empty if the error comes after the header); EIG_ERR_BREAKDOWN if the
+ * loaded H is not positive definite. */
+eig_status eig_basis_load(eig_basis basis, const char *path, void *stream);
 
 /* Kernel instrumentation (diagnostics; the paper reports only per-phase wall
  * times, Table 1).  Every kernel launch of the library is counted per kernel name

@@ -24,6 +24,7 @@ EIG_ERR_BUDGET = -3
 EIG_ERR_CUDA = -4
 EIG_ERR_BREAKDOWN = -5
 EIG_ERR_TIMEOUT = -6
+EIG_ERR_IO = -7
 
 PREC = {"f64": 64, "f32": 32, "f16": 16, 64: 64, 32: 32, 16: 16}
 
@@ -36,7 +37,7 @@ class EigError(RuntimeError):
 
 class OpOpts(ctypes.Structure):
     _fields_ = [("spinor_prec", ctypes.c_int), ("link_compress12", ctypes.c_int), ("max_rhs", ctypes.c_int),
-                ("reliable_delta", ctypes.c_double)]
+                ("reliable_delta", ctypes.c_double), ("even_odd", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -61,17 +62,22 @@ SIGNATURES = {
     "eig_op_create": [_P, _P, _D, _P, _P],
     "eig_op_destroy": [_P],
     "eig_op_apply": [_P, _I, _P, _P, _I, _P],
+    "eig_op_stencil_choice": [_P, _I, _P, _P],
     "eig_basis_create": [_P, _I, _P],
     "eig_basis_destroy": [_P],
     "eig_basis_size": [_P, _P],
     "eig_basis_truncate": [_P, _I],
     "eig_eigcg_solve": [_P, _P, _P, _P, _I, _I, _D, _I, _P, _P],
+    "eig_eigcg_solve_sp": [_P, _P, _P, _P, _I, _I, _D, _I, _I, _D, _P, _P],
     "eig_basis_grow": [_P, _P],
     "eig_basis_deflate": [_P, _P, _P, _P, _I, _P],
     "eig_initcg_solve": [_P, _P, _P, _P, _D, _D, _I, _I, _P, _P],
     "eig_basis_ritz": [_P, _P, _P, _P, _P],
     "eig_basis_vector": [_P, _I, _P, _P],
     "eig_basis_h": [_P, _P],
+    "eig_basis_pending": [_P, _P, _P],
+    "eig_basis_save": [_P, ctypes.c_char_p, _P],
+    "eig_basis_load": [_P, ctypes.c_char_p, _P],
     "eig_profile_enable": [_I],
     "eig_profile_reset": [],
     "eig_profile_read": [_P, _I, _P],
@@ -142,10 +148,10 @@ def _stream(stream) -> int:
 # functions with the C names
 # ------------------------------------------------------------------------------------------
 def eig_op_create(gauge: np.ndarray, dims, m_q: float, spinor_prec=64, link_compress12=1, max_rhs=1,
-                  reliable_delta=0.1) -> ctypes.c_void_p:
+                  reliable_delta=0.1, even_odd=0) -> ctypes.c_void_p:
     g = np.ascontiguousarray(gauge, dtype=np.complex128)
     d = (ctypes.c_int * 4)(*[int(v) for v in dims])
-    opts = OpOpts(PREC[spinor_prec], int(link_compress12), int(max_rhs), float(reliable_delta))
+    opts = OpOpts(PREC[spinor_prec], int(link_compress12), int(max_rhs), float(reliable_delta), int(even_odd))
     h = ctypes.c_void_p()
     _check(load().eig_op_create(g.ctypes.data, d, float(m_q), ctypes.byref(opts), ctypes.byref(h)))
     return h
@@ -157,6 +163,14 @@ def eig_op_destroy(op) -> None:
 
 def eig_op_apply(op, which: int, vin, vout, k: int = 1, stream=None) -> None:
     _check(load().eig_op_apply(op, int(which), _ptr(vin), _ptr(vout), int(k), _stream(stream)))
+
+
+def eig_op_stencil_choice(op, k: int = 1):
+    """(variant, link_reals) the stencil autotuner chose for k-RHS products; (-1, 0)
+    for FP64 ops or before the first solve with k RHS."""
+    v, g = ctypes.c_int(), ctypes.c_int()
+    _check(load().eig_op_stencil_choice(op, int(k), ctypes.byref(v), ctypes.byref(g)))
+    return v.value, g.value
 
 
 def eig_basis_create(op, max_vecs: int) -> ctypes.c_void_p:
@@ -183,6 +197,17 @@ def eig_eigcg_solve(op, basis, b, x, nev: int, m: int, tol: float, max_iter: int
     st = Stats()
     status = _check(load().eig_eigcg_solve(op, basis, _ptr(b), _ptr(x), int(nev), int(m), float(tol),
                                            int(max_iter), ctypes.byref(st), _stream(stream)))
+    d = st.as_dict()
+    d["status"] = status
+    return d
+
+
+def eig_eigcg_solve_sp(op, basis, b, x, nev: int, m: int, tol: float, sp_vecs: int, sp_shift: float,
+                       max_iter: int = 100000, stream=None):
+    st = Stats()
+    status = _check(load().eig_eigcg_solve_sp(op, basis, _ptr(b), _ptr(x), int(nev), int(m), float(tol),
+                                              int(max_iter), int(sp_vecs), float(sp_shift), ctypes.byref(st),
+                                              _stream(stream)))
     d = st.as_dict()
     d["status"] = status
     return d
@@ -226,6 +251,22 @@ def eig_basis_h(basis) -> np.ndarray:
     out = np.zeros((l, l), dtype=np.complex128)
     _check(load().eig_basis_h(basis, out.ctypes.data))
     return out
+
+
+def eig_basis_pending(basis) -> np.ndarray:
+    n = ctypes.c_int()
+    _check(load().eig_basis_pending(basis, None, ctypes.byref(n)))
+    ev = np.zeros(n.value)
+    _check(load().eig_basis_pending(basis, ev.ctypes.data, ctypes.byref(n)))
+    return ev
+
+
+def eig_basis_save(basis, path, stream=None) -> None:
+    _check(load().eig_basis_save(basis, os.fsencode(path), _stream(stream)))
+
+
+def eig_basis_load(basis, path, stream=None) -> None:
+    _check(load().eig_basis_load(basis, os.fsencode(path), _stream(stream)))
 
 
 def eig_profile_enable(on: bool = True) -> None:

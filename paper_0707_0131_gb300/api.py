@@ -17,13 +17,16 @@ from . import _lib
 
 
 class Op:
-    def __init__(self, gauge, dims, m_q, prec=64, compress12=True, max_rhs=1, reliable_delta=0.1):
+    def __init__(self, gauge, dims, m_q, prec=64, compress12=True, max_rhs=1, reliable_delta=0.1, even_odd=False):
         self.dims = tuple(int(d) for d in dims)
         self.V = int(np.prod(self.dims))
+        self.even_odd = bool(even_odd)
+        self.Vf = self.V // 2 if self.even_odd else self.V  # sites of apply / basis vectors
         self.m_q = float(m_q)
         self.prec = _lib.PREC[prec]
         self.max_rhs = int(max_rhs)
-        self.h = _lib.eig_op_create(gauge, self.dims, m_q, prec, 1 if compress12 else 0, max_rhs, reliable_delta)
+        self.h = _lib.eig_op_create(gauge, self.dims, m_q, prec, 1 if compress12 else 0, max_rhs, reliable_delta,
+                                    1 if self.even_odd else 0)
 
     def close(self):
         if self.h is not None:
@@ -39,6 +42,10 @@ class Op:
     def apply(self, which, vin, vout, k=1, stream=None):
         _lib.eig_op_apply(self.h, which, vin, vout, k, stream)
         return vout
+
+    def stencil_choice(self, k=1):
+        """(variant, link_reals) the autotuner chose for k-RHS stencils."""
+        return _lib.eig_op_stencil_choice(self.h, k)
 
     def _host(self, which, psi, k):
         vin = np.ascontiguousarray(psi, dtype=np.complex128)
@@ -57,6 +64,10 @@ class Op:
     def eigcg_solve(self, b, x, nev, m, tol, basis=None, max_iter=100000, stream=None):
         return _lib.eig_eigcg_solve(self.h, basis.h if basis is not None else None, b, x, nev, m, tol, max_iter,
                                     stream)
+
+    def eigcg_solve_sp(self, b, x, nev, m, tol, basis, sp_vecs, sp_shift, max_iter=100000, stream=None):
+        """eigCG preconditioned by the spectral preconditioner of basis' first sp_vecs vectors."""
+        return _lib.eig_eigcg_solve_sp(self.h, basis.h, b, x, nev, m, tol, sp_vecs, sp_shift, max_iter, stream)
 
     def initcg_solve(self, b, x, tol, restart_tol=0.0, basis=None, k=1, max_iter=100000, stream=None):
         return _lib.eig_initcg_solve(self.h, basis.h if basis is not None else None, b, x, tol, restart_tol,
@@ -97,7 +108,7 @@ class Basis:
         return _lib.eig_basis_ritz(self.h, residuals, stream)
 
     def vector(self, j):
-        out = np.zeros(self.op.V * 12, dtype=np.complex128)
+        out = np.zeros(self.op.Vf * 12, dtype=np.complex128)
         _lib.eig_basis_vector(self.h, j, out)
         return out
 
@@ -106,3 +117,15 @@ class Basis:
 
     def H(self):
         return _lib.eig_basis_h(self.h)
+
+    def pending(self):
+        """Ritz values of the pending block of the last eigCG solve."""
+        return _lib.eig_basis_pending(self.h)
+
+    def save(self, path, stream=None):
+        """Writes U and H to a file (the pending Ritz block is not saved)."""
+        _lib.eig_basis_save(self.h, path, stream)
+
+    def load(self, path, stream=None):
+        """Replaces U and H with a saved basis of the same operator."""
+        _lib.eig_basis_load(self.h, path, stream)

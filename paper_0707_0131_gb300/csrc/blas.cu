@@ -60,6 +60,37 @@ __global__ void k_unpack(FieldView f, double2 *__restrict__ nat) {
     }
 }
 
+// full-lattice FP64 field <-> half-lattice FP64 field of the sites of one parity
+// (site s of parity p(x) = (x + y + z + t) mod 2 at half index s / 2; Lx even)
+__global__ void k_parity_move(FieldView full, FieldView half, int parity, int L0, int L1, int L2, int to_half) {
+    const long total = half.V * half.k;
+    for (long g = (long)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += (long)gridDim.x * blockDim.x) {
+        const long h = g / half.k;
+        const int r = (int)(g - h * half.k);
+        const long lh = L0 / 2, rest = h / lh;
+        const int y = (int)(rest % L1), z = (int)((rest / L1) % L2), t = (int)(rest / ((long)L1 * L2));
+        const long s = 2 * (h % lh) + ((parity + y + z + t) & 1) + L0 * rest;
+        Spinor<double> v;
+        if (to_half) {
+            SpinorStore<double>::load(full, s, r, v);
+            SpinorStore<double>::store(half, h, r, v);
+        } else {
+            SpinorStore<double>::load(half, h, r, v);
+            SpinorStore<double>::store(full, s, r, v);
+        }
+    }
+}
+
+cudaError_t launch_parity_move(Field full, Field half, int parity, const int L[4], bool to_half, cudaStream_t s) {
+    if (full.prec != P64 || half.prec != P64 || full.v.k != half.v.k || half.v.V * 2 != full.v.V || (L[0] & 1))
+        return cudaErrorInvalidValue;
+    ProfScope prof("parity_move", (double)half.v.V * half.v.k * 2 * 192.0, s);
+    const int B = 128;
+    k_parity_move<<<stream_grid(half.v.V * half.v.k, B), B, 0, s>>>(full.v, half.v, parity, L[0], L[1], L[2],
+                                                                    to_half ? 1 : 0);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_pack(const double *nat, Field f, cudaStream_t s) {
     ProfScope prof("pack", (double)f.v.V * f.v.k * (192.0 + spb(f.prec)), s);
     const int B = 128;
@@ -240,6 +271,89 @@ __global__ void __launch_bounds__(256) k_norm2(FieldView f, CGScalars *st, int a
             if (h_rho) h_rho[(long)iter * k + r] = tot;
         }
     });
+}
+
+// ---------------------------------------------------------------------------------------
+// Spectral preconditioner z = P^{-1} r = r + U (G (U^H r)) (Sec. 2), G = shift H^{-1} - I:
+// the coefficients y = G c of one RHS, and rho = r^H z with the CG scalars of Fig. 1
+// steps 3-4, 8 (preconditioned form)
+// ---------------------------------------------------------------------------------------
+__global__ void k_sp_coef(const double *G, const double *C, double *Y, int l) {
+    for (int a = threadIdx.x; a < l; a += blockDim.x) {
+        double re = 0.0, im = 0.0;
+        for (int b = 0; b < l; b++) {
+            const double gr = G[2 * ((long)a * l + b)], gi = G[2 * ((long)a * l + b) + 1];
+            const double cr = C[2 * b], ci = C[2 * b + 1];
+            re += gr * cr - gi * ci;
+            im += gr * ci + gi * cr;
+        }
+        Y[2 * a] = re;
+        Y[2 * a + 1] = im;
+    }
+}
+
+cudaError_t launch_sp_coef(const double *G, const double *C, double *Y, int l, cudaStream_t s) {
+    ProfScope prof("sp_coef", (double)l * l * 16.0, s);
+    k_sp_coef<<<1, 256, 0, s>>>(G, C, Y, l);
+    return cudaGetLastError();
+}
+
+template <typename S>
+__global__ void __launch_bounds__(256) k_pcg_rho(FieldView r, FieldView z, CGScalars *st, double *h_rho,
+                                                 double *h_beta, int iter, double *partials, unsigned *counter) {
+    using C = typename SpinorStore<S>::C;
+    __shared__ double smem[(256 / 32) * MAX_RHS];
+    const long total = r.V * r.k;
+    double n = 0.0;
+    for (long g = (long)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += (long)gridDim.x * blockDim.x) {
+        const long s = g / r.k;
+        const int q = (int)(g - s * r.k);
+        Spinor<C> a, b;
+        SpinorStore<S>::load(r, s, q, a);
+        SpinorStore<S>::load(z, s, q, b);
+        C d = 0;
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) d += a.s[i][j].re * b.s[i][j].re + a.s[i][j].im * b.s[i][j].im;
+        n += (double)d;
+    }
+    const double bs = block_reduce_rhs(n, r.k, smem);
+    const int k = r.k;
+    grid_reduce_rhs(bs, k, partials, counter, smem, [=](int q, double tot) {
+        CGScalars &c = st[q];
+        if (!c.active) return;
+        if (!(tot > 0.0) || !isfinite(tot)) {  // P^{-1} not positive definite on r
+            c.breakdown = 1;
+            c.active = 0;
+            return;
+        }
+        c.rho = tot;  // step 4: rho = r^H z
+        h_rho[(long)iter * k + q] = tot;
+        if (iter >= 1) {  // step 8: beta = rho / rho_prev (rho_prev moved by the CG epilogue)
+            c.beta = tot / c.rho_prev;
+            h_beta[(long)(iter + 1) * k + q] = c.beta;
+        }
+    });
+}
+
+cudaError_t launch_pcg_rho(Field r, Field z, CGScalars *st, History h, int iter, RedScratch red, cudaStream_t s) {
+    ProfScope prof("pcg_rho", (double)r.v.V * r.v.k * 2.0 * spb(r.prec), s);
+    if (z.prec != r.prec || z.v.V != r.v.V || z.v.k != r.v.k) return cudaErrorInvalidValue;
+    const int B = 256;
+    int G = stream_grid(r.v.V * r.v.k, B);
+    if (G > red.max_blocks) G = red.max_blocks;
+    switch (r.prec) {
+        case P64:
+            k_pcg_rho<double><<<G, B, 0, s>>>(r.v, z.v, st, h.rho, h.beta, iter, red.partials, red.counter);
+            break;
+        case P32:
+            k_pcg_rho<float><<<G, B, 0, s>>>(r.v, z.v, st, h.rho, h.beta, iter, red.partials, red.counter);
+            break;
+        case P16:
+            return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_norm2(Field f, CGScalars *st, bool as_rho, History h, int iter, RedScratch red, cudaStream_t s) {

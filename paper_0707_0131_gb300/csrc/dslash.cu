@@ -18,6 +18,7 @@
 // every chunk load coalesced and lets the k RHS of one site share each link load
 // through L1.  Grids are persistent (a multiple of the SM count), with
 // grid-stride loops.
+#include <string>
 #include <cstring>
 #include <mutex>
 #include <unordered_map>
@@ -31,11 +32,14 @@ enum Epi { EPI_PLAIN = 0, EPI_NORM = 1, EPI_CG = 2, EPI_RESID = 3 };
 
 struct KArgs {
     FieldView in, out, p, x, r, tsave, b;
+    FieldView cen;     // centre-term input (odd-even form), else in
     GaugeView g;
     int L0, L1, L2, L3;
-    long V;
+    long V;            // output sites (V / 2 in the odd-even form)
     int k;
     double diag;
+    double hcoef;      // coefficient of the hop sum (-1/2 for M)
+    int eo;            // output parity (odd-even form) or -1
     int store_out, save_t, set_rho;
     CGScalars *st;
     double *h_alpha, *h_beta, *h_rho;
@@ -131,8 +135,10 @@ __device__ __forceinline__ void mul_link_dag(const Link<C> &U, const Half<C> &h,
         }
 }
 
+// hop of direction MU: spinors at field indices sf (x + mu) and sb (x - mu), links at
+// lattice sites s (U_mu(x)) and lb (U_mu(x - mu))
 template <int MU, typename S, int GF, bool DAG>
-__device__ __forceinline__ void hop_dir(const KArgs &a, long s, long sf, long sb, int r,
+__device__ __forceinline__ void hop_dir(const KArgs &a, long s, long lb, long sf, long sb, int r,
                                         Spinor<typename SpinorStore<S>::C> &acc) {
     using C = typename SpinorStore<S>::C;
     constexpr int SF = DAG ? +1 : -1;  // forward projector  I + SF g_mu
@@ -147,40 +153,61 @@ __device__ __forceinline__ void hop_dir(const KArgs &a, long s, long sf, long sb
     accumulate<MU, SF>(acc, uh);
     SpinorStore<S>::load(a.in, sb, r, nb);
     project<MU, SB>(nb, h);
-    GaugeLoad<GF>::load(a.g, MU, sb, U);
+    GaugeLoad<GF>::load(a.g, MU, lb, U);
     mul_link_dag(U, h, uh);
     accumulate<MU, SB>(acc, uh);
 }
 
+// out = diag * centre + hcoef * (hop sum) at output site s (a half-lattice index in the
+// odd-even form: the site of parity a.eo at s, with x = 2 (s mod Lx/2) + parity bit)
 template <typename S, int GF, bool DAG>
 __device__ __forceinline__ void wilson_site(const KArgs &a, long s, int r, Spinor<typename SpinorStore<S>::C> &out) {
     using C = typename SpinorStore<S>::C;
     const long s1 = a.L0, s2 = (long)a.L0 * a.L1, s3 = s2 * a.L2;
-    const int x = (int)(s % a.L0);
-    const int y = (int)((s / s1) % a.L1);
-    const int z = (int)((s / s2) % a.L2);
-    const int t = (int)(s / s3);
+    int x, y, z, t;
+    long sl = s;  // lattice site
+    if (a.eo >= 0) {
+        const long lh = a.L0 / 2, rest = s / lh;
+        y = (int)(rest % a.L1);
+        z = (int)((rest / a.L1) % a.L2);
+        t = (int)(rest / ((long)a.L1 * a.L2));
+        x = (int)(2 * (s % lh) + ((a.eo + y + z + t) & 1));
+        sl = x + a.L0 * rest;
+    } else {
+        x = (int)(s % a.L0);
+        y = (int)((s / s1) % a.L1);
+        z = (int)((s / s2) % a.L2);
+        t = (int)(s / s3);
+    }
+    const long nf[4] = {x == a.L0 - 1 ? sl - (a.L0 - 1) : sl + 1, y == a.L1 - 1 ? sl - (a.L1 - 1) * s1 : sl + s1,
+                        z == a.L2 - 1 ? sl - (a.L2 - 1) * s2 : sl + s2, t == a.L3 - 1 ? sl - (a.L3 - 1) * s3 : sl + s3};
+    const long nb[4] = {x == 0 ? sl + (a.L0 - 1) : sl - 1, y == 0 ? sl + (a.L1 - 1) * s1 : sl - s1,
+                        z == 0 ? sl + (a.L2 - 1) * s2 : sl - s2, t == 0 ? sl + (a.L3 - 1) * s3 : sl - s3};
+    const int sh = a.eo >= 0 ? 1 : 0;  // neighbours are of the other parity: field index = site / 2
     Spinor<C> acc;
 #pragma unroll
     for (int i = 0; i < 4; i++)
 #pragma unroll
         for (int j = 0; j < 3; j++) acc.s[i][j] = cmk<C>(0, 0);
-    hop_dir<0, S, GF, DAG>(a, s, x == a.L0 - 1 ? s - (a.L0 - 1) : s + 1, x == 0 ? s + (a.L0 - 1) : s - 1, r, acc);
-    hop_dir<1, S, GF, DAG>(a, s, y == a.L1 - 1 ? s - (a.L1 - 1) * s1 : s + s1,
-                           y == 0 ? s + (a.L1 - 1) * s1 : s - s1, r, acc);
-    hop_dir<2, S, GF, DAG>(a, s, z == a.L2 - 1 ? s - (a.L2 - 1) * s2 : s + s2,
-                           z == 0 ? s + (a.L2 - 1) * s2 : s - s2, r, acc);
-    hop_dir<3, S, GF, DAG>(a, s, t == a.L3 - 1 ? s - (a.L3 - 1) * s3 : s + s3,
-                           t == 0 ? s + (a.L3 - 1) * s3 : s - s3, r, acc);
+    hop_dir<0, S, GF, DAG>(a, sl, nb[0], nf[0] >> sh, nb[0] >> sh, r, acc);
+    hop_dir<1, S, GF, DAG>(a, sl, nb[1], nf[1] >> sh, nb[1] >> sh, r, acc);
+    hop_dir<2, S, GF, DAG>(a, sl, nb[2], nf[2] >> sh, nb[2] >> sh, r, acc);
+    hop_dir<3, S, GF, DAG>(a, sl, nb[3], nf[3] >> sh, nb[3] >> sh, r, acc);
     Spinor<C> c0;
-    SpinorStore<S>::load(a.in, s, r, c0);
+    if (a.eo < 0) SpinorStore<S>::load(a.in, s, r, c0);
+    else if (a.diag != 0.0) SpinorStore<S>::load(a.cen, s, r, c0);
+    else
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) c0.s[i][j] = cmk<C>(0, 0);  // hops only
     const C d = (C)a.diag;
-    const C h = (C)0.5;
+    const C h = (C)a.hcoef;
 #pragma unroll
     for (int i = 0; i < 4; i++)
 #pragma unroll
-        for (int j = 0; j < 3; j++) out.s[i][j] = cmk<C>(d * c0.s[i][j].re - h * acc.s[i][j].re,
-                                                         d * c0.s[i][j].im - h * acc.s[i][j].im);
+        for (int j = 0; j < 3; j++) out.s[i][j] = cmk<C>(d * c0.s[i][j].re + h * acc.s[i][j].re,
+                                                         d * c0.s[i][j].im + h * acc.s[i][j].im);
 }
 
 template <typename C>
@@ -359,9 +386,12 @@ static KArgs base_args(const DslashCall &c) {
     a.L1 = c.L[1];
     a.L2 = c.L[2];
     a.L3 = c.L[3];
-    a.V = c.V;
+    a.eo = c.eo_parity;
+    a.V = c.eo_parity >= 0 ? c.V / 2 : c.V;
     a.k = c.k;
     a.diag = c.diag;
+    a.hcoef = c.hcoef;
+    if (c.eo_parity >= 0) a.cen = c.cen.v;
     return a;
 }
 
@@ -382,22 +412,28 @@ static double dslash_bytes(const DslashCall &c, const KArgs &a) {
     double per_rhs = 2 * sp;                                                 // in + out
     if (EPI == EPI_CG) per_rhs = sp + 2 * sp + (a.save_t ? w : 0);           // u, r rw, t
     if (EPI == EPI_RESID) per_rhs = 3 * sp;                                  // u, b, r
-    return (double)c.V * (site_bytes_gauge(c.gformat) + c.k * per_rhs);
+    if (c.eo_parity >= 0 && c.diag != 0.0) per_rhs += sp;                    // centre field
+    // every link once (the odd-even form touches all links for half the sites)
+    return (double)c.V * site_bytes_gauge(c.gformat) + (double)a.V * c.k * per_rhs;
 }
 
-static const char *dslash_name(int epi, Prec p) {
+// Profile name: epilogue, storage precision and, for batched launches, the batch width
+// (the single-RHS and batched stencils have different rooflines).
+static std::string dslash_name(int epi, Prec p, int k) {
     static const char *names[4][3] = {{"dslash_f64", "dslash_f32", "dslash_f16"},
                                       {"dslash_norm_f64", "dslash_norm_f32", "dslash_norm_f16"},
                                       {"dslash_cg_f64", "dslash_cg_f32", "dslash_cg_f16"},
                                       {"dslash_resid_f64", "dslash_resid_f32", "dslash_resid_f16"}};
-    return names[epi][p];
+    std::string n = names[epi][p];
+    if (k > 1) n += "_k" + std::to_string(k);
+    return n;
 }
 
 template <int EPI>
 static cudaError_t dispatch(const DslashCall &c, KArgs &a, int cap, cudaStream_t s) {
-    const long work = c.V * c.k;
+    const long work = a.V * c.k;
     const int block = 128;
-    ProfScope prof(dslash_name(EPI, c.in.prec), dslash_bytes<EPI>(c, a), s);
+    ProfScope prof(dslash_name(EPI, c.in.prec, c.k).c_str(), dslash_bytes<EPI>(c, a), s);
 #define EIG_LAUNCH(S, GF)                                                                   \
     do {                                                                                    \
         if (c.dagger) {                                                                     \
@@ -430,7 +466,7 @@ static cudaError_t dispatch(const DslashCall &c, KArgs &a, int cap, cudaStream_t
 cudaError_t launch_dslash(const DslashCall &c, cudaStream_t s) {
     KArgs a = base_args(c);
     if (c.in.prec != P64) {
-        ProfScope prof(dslash_name(EPI_PLAIN, c.in.prec), dslash_bytes<EPI_PLAIN>(c, a), s);
+        ProfScope prof(dslash_name(EPI_PLAIN, c.in.prec, c.k).c_str(), dslash_bytes<EPI_PLAIN>(c, a), s);
         return launch_dslash32(c, s);
     }
     return dispatch<EPI_PLAIN>(c, a, 0, s);
@@ -448,7 +484,7 @@ cudaError_t launch_dslash_norm(const DslashCall &c, CGScalars *st, History h, in
     a.partials = red.partials;
     a.counter = red.counter;
     if (c.in.prec != P64) {
-        ProfScope prof(dslash_name(EPI_NORM, c.in.prec), dslash_bytes<EPI_NORM>(c, a), s);
+        ProfScope prof(dslash_name(EPI_NORM, c.in.prec, c.k).c_str(), dslash_bytes<EPI_NORM>(c, a), s);
         return launch_dslash32_norm(c, st, h, iter, red, s);
     }
     return dispatch<EPI_NORM>(c, a, red.max_blocks, s);
@@ -469,7 +505,7 @@ cudaError_t launch_dslash_cg(const DslashCall &c, Field r, Field t_save, CGScala
     a.partials = red.partials;
     a.counter = red.counter;
     if (c.in.prec != P64) {
-        ProfScope prof(dslash_name(EPI_CG, c.in.prec), dslash_bytes<EPI_CG>(c, a), s);
+        ProfScope prof(dslash_name(EPI_CG, c.in.prec, c.k).c_str(), dslash_bytes<EPI_CG>(c, a), s);
         return launch_dslash32_cg(c, r, t_save, st, h, iter, red, s);
     }
     return dispatch<EPI_CG>(c, a, red.max_blocks, s);

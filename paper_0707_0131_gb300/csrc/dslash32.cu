@@ -21,15 +21,59 @@ std::unordered_map<const void *, int> g_occ32;
 //   2  direct loads, 1 RHS per thread, 4 blocks/SM         3  direct, 1 RHS, 5 blocks/SM
 //   4  direct loads, 2 RHS per thread, 3 blocks/SM         5  direct, 2 RHS, 4 blocks/SM
 //   6  as 4, with an L1 prefetch of the next hop           7  as 3, with the L1 prefetch
+//   8 + v (v = 2..7): direct variant v over the tiled site traversal (full lattice only;
+//   v itself where the lattice cannot be tiled)
 // The fastest valid one is chosen per (volume, k, storage, link format) by
-// autotune_dslash32 and cached; EIG_DSLASH_VARIANT=0..7 in the environment forces one.
-constexpr int NVAR = 8;
+// autotune_dslash32 and cached; EIG_DSLASH_VARIANT=0..15 in the environment forces one.
+constexpr int NVAR = 16;
 
-int variant_rb(int v) { return (v == 1 || v == 4 || v == 5 || v == 6) ? 2 : 1; }
+int variant_rb(int v) {
+    v &= 7;
+    return (v == 1 || v == 4 || v == 5 || v == 6) ? 2 : 1;
+}
 
 bool variant_ok(int v, unsigned k, int gf) {
     if (v < 0 || v >= NVAR) return false;
+    if (v >= 8 && (v & 7) < 2) return false;  // tiling only for the direct variants
     if (variant_rb(v) == 2 && (k < 2 || (k % 2) != 0)) return false;
+    return true;
+}
+
+// Tiled traversal for a launch with rb RHS per thread: a tile of as many sites as a CTA
+// covers (TPB / (k / rb), a power of two), its extents doubled round-robin from x while
+// each divides its lattice extent and leaves at least two tiles along it.  False (and
+// a.tile = 0) for the odd-even form or where no such tile exists.
+bool tile_setup(K32 &a, int rb) {
+    a.tile = 0;
+    if (a.eo >= 0) return false;
+    const unsigned kb = a.k / (unsigned)rb;
+    if (kb == 0 || kb > (unsigned)TPB) return false;
+    unsigned b = 0;
+    while ((1u << (b + 1)) <= (unsigned)TPB / kb) b++;
+    const unsigned L[4] = {a.L0, a.L1, a.L2, a.L3};
+    unsigned tl[4] = {0, 0, 0, 0};
+    while (b > 0) {
+        bool grew = false;
+        for (int d = 0; d < 4 && b > 0; d++) {
+            const unsigned e = 2u << tl[d];
+            if (L[d] % e == 0 && L[d] / e >= 2) {
+                tl[d]++;
+                b--;
+                grew = true;
+            }
+        }
+        if (!grew) return false;
+    }
+    a.tl0 = tl[0];
+    a.tl1 = tl[1];
+    a.tl2 = tl[2];
+    a.tl3 = tl[3];
+    a.nt0 = a.L0 >> tl[0];
+    a.nt1 = a.L1 >> tl[1];
+    a.dt0 = fastdiv_make(a.nt0);
+    a.dt1 = fastdiv_make(a.nt1);
+    a.dt2 = fastdiv_make(a.L2 >> tl[2]);
+    a.tile = 1;
     return true;
 }
 
@@ -44,14 +88,27 @@ int forced_variant() {
     static int f = -2;
     if (f == -2) {
         const char *e = getenv("EIG_DSLASH_VARIANT");
-        f = (e && e[0] >= '0' && e[0] < '0' + NVAR && e[1] == 0) ? e[0] - '0' : -1;
+        char *end = nullptr;
+        const long v = e ? strtol(e, &end, 10) : -1;
+        f = (e && end != e && *end == 0 && v >= 0 && v < NVAR) ? (int)v : -1;
     }
     return f;
 }
 
 thread_local int g_var_override = -1;  // set while autotuning
 
+int variant_for_full(const K32 &a, int prec, int gf);
+
 int variant_for(const K32 &a, int prec, int gf) {
+    // the staged variants take the centre term from `in`: not for the odd-even form
+    if (a.eo >= 0) {
+        const int v = variant_for_full(a, prec, gf);
+        return v <= 1 ? (variant_ok(4, a.k, gf) ? 4 : 2) : v;
+    }
+    return variant_for_full(a, prec, gf);
+}
+
+int variant_for_full(const K32 &a, int prec, int gf) {
     if (g_var_override >= 0 && variant_ok(g_var_override, a.k, gf)) return g_var_override;
     const int f = forced_variant();
     if (f >= 0 && variant_ok(f, a.k, gf)) return f;
@@ -86,8 +143,10 @@ cudaError_t launch_rb(const K32 &a, int cap, cudaStream_t s) {
     const int prec = sizeof(S) == 4 ? 32 : 16;
     const int v = variant_for(a, prec, GF);
     if (v <= 1) return launch_staged<S, GF, DAG, EPI>(variant_rb(v), a, cap, s);
-    if (variant_rb(v) == 1) return d32_launch_direct_rb1(v, prec, GF, DAG, EPI, a, cap, s);
-    return d32_launch_direct_rb2(v, prec, GF, DAG, EPI, a, cap, s);
+    K32 b = a;
+    if (v >= 8) tile_setup(b, variant_rb(v));
+    if (variant_rb(v) == 1) return d32_launch_direct_rb1(v & 7, prec, GF, DAG, EPI, b, cap, s);
+    return d32_launch_direct_rb2(v & 7, prec, GF, DAG, EPI, b, cap, s);
 }
 
 template <int EPI>
@@ -119,10 +178,19 @@ K32 args32(const DslashCall &c) {
     a.d0 = fastdiv_make(a.L0);
     a.d1 = fastdiv_make(a.L1);
     a.d2 = fastdiv_make(a.L2);
-    a.V = (unsigned)c.V;
+    a.Vg = (unsigned)c.V;
+    a.eo = c.eo_parity;
+    a.V = (unsigned)(c.eo_parity >= 0 ? c.V / 2 : c.V);
     a.k = (unsigned)c.k;
-    a.P = (unsigned)(c.V * c.k);
+    a.P = a.V * a.k;
     a.diag = (float)c.diag;
+    a.hcoef = (float)c.hcoef;
+    a.lh = a.L0 / 2;
+    if (a.lh >= 2) a.dh = fastdiv_make(a.lh);
+    if (c.eo_parity >= 0) {
+        a.cen = static_cast<const float4 *>(c.cen.v.data);
+        a.cen_s = c.cen.v.scale;
+    }
     return a;
 }
 
@@ -174,6 +242,20 @@ int dslash32_best_gformat(long V, int k, int prec) {
     return it == g_fmt.end() ? -1 : it->second;
 }
 
+// The choice a call would be launched with: link format (-1 before the call's shape is
+// tuned) and stencil variant.
+int dslash32_choice(const DslashCall &c0, int *variant) {
+    const int prec = c0.in.prec == P32 ? 32 : 16;
+    *variant = -1;
+    const int gf = dslash32_best_gformat(c0.V, c0.k, prec);
+    if (gf < 0) return -1;
+    DslashCall c = c0;
+    c.gformat = gf;
+    const K32 a = args32(c);
+    *variant = variant_for(a, prec, gf);
+    return gf;
+}
+
 // Times the plain stencil in every valid variant on the caller's buffers (in -> out),
 // for the call's link format and the alternative one, and caches the fastest choices.
 cudaError_t autotune_dslash32(const DslashCall &c0, const void *const *gauge_alts, const int *gf_alts, int n_alts,
@@ -202,6 +284,8 @@ cudaError_t autotune_dslash32(const DslashCall &c0, const void *const *gauge_alt
         int best_v = -1;
         for (int v = 0; v < NVAR; v++) {
             if (!variant_ok(v, a.k, c.gformat)) continue;
+            K32 tb = a;
+            if (v >= 8 && !tile_setup(tb, variant_rb(v))) continue;  // same as v - 8 here
             if (forced_variant() >= 0 && v != forced_variant()) continue;
             g_var_override = v;
             dispatch32<E_PLAIN>(c, a, 0, s);  // warm

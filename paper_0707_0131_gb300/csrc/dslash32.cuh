@@ -37,8 +37,22 @@ struct K32 {
     float4 *x;     // FP32 x (always FP32 storage)
     float4 *tsave; // FP32, k = 1
     const void *g;
-    unsigned L0, L1, L2, L3, V;
+    unsigned L0, L1, L2, L3, V;  // V: output sites (V / 2 in the odd-even form)
+    unsigned Vg;                 // lattice sites: stride of the link planes
     FastDiv d0, d1, d2;  // division by L0, L1, L2
+    // odd-even form: output parity (or -1), centre-term input, hop coefficient
+    int eo;
+    unsigned lh;         // L0 / 2
+    FastDiv dh;          // division by L0 / 2 (lh >= 2)
+    const float4 *cen;
+    const float *cen_s;
+    float hcoef;
+    // tiled traversal (full lattice, tile != 0): consecutive output sites run through
+    // blocks of 2^tl0 x 2^tl1 x 2^tl2 x 2^tl3 lattice sites, the blocks in lexicographic
+    // order (nt0 x nt1 x nt2 per t-slab), so that a CTA's sites are each other's
+    // neighbours and more hop loads hit L1
+    unsigned tile, tl0, tl1, tl2, tl3, nt0, nt1;
+    FastDiv dt0, dt1, dt2;
     unsigned k;    // RHS per field
     unsigned P;    // V * k (chunk plane stride in vector elements)
     float diag;
@@ -347,19 +361,19 @@ struct Pipe {
         }
         if (with_link) {
             if (GF == GF_F32_12) {
-                const float4 *g = static_cast<const float4 *>(a.g) + (unsigned)mu * 3u * a.V;
+                const float4 *g = static_cast<const float4 *>(a.g) + (unsigned)mu * 3u * a.Vg;
 #pragma unroll
-                for (int c = 0; c < 3; c++) cpa16(slot(st, RB * NSP + c), g + c * a.V + ls);
+                for (int c = 0; c < 3; c++) cpa16(slot(st, RB * NSP + c), g + c * a.Vg + ls);
             } else if (GF == GF_F32_18) {
-                const float2 *g = static_cast<const float2 *>(a.g) + (unsigned)mu * 9u * a.V;
+                const float2 *g = static_cast<const float2 *>(a.g) + (unsigned)mu * 9u * a.Vg;
 #pragma unroll
                 for (int e = 0; e < 9; e++)
-                    cpa8(reinterpret_cast<float2 *>(slot(st, RB * NSP + e / 2)) + (e & 1), g + e * a.V + ls);
+                    cpa8(reinterpret_cast<float2 *>(slot(st, RB * NSP + e / 2)) + (e & 1), g + e * a.Vg + ls);
             } else {
-                const uint2 *g = static_cast<const uint2 *>(a.g) + (unsigned)mu * 3u * a.V;
+                const uint2 *g = static_cast<const uint2 *>(a.g) + (unsigned)mu * 3u * a.Vg;
 #pragma unroll
                 for (int c = 0; c < 3; c++)
-                    cpa8(reinterpret_cast<uint2 *>(slot(st, RB * NSP + c / 2)) + (c & 1), g + c * a.V + ls);
+                    cpa8(reinterpret_cast<uint2 *>(slot(st, RB * NSP + c / 2)) + (c & 1), g + c * a.Vg + ls);
             }
         }
         cpa_commit();
@@ -440,7 +454,7 @@ template <int MU, int SG, bool DAGGER, typename S, int GF, int RB>
 __device__ __forceinline__ void hop_direct(const K32 &a, unsigned ns, unsigned ls, unsigned r0, unsigned rstride,
                                            Sp *acc) {
     Lk U;
-    Link32<GF>::load(a.g, a.V, MU, ls, U);
+    Link32<GF>::load(a.g, a.Vg, MU, ls, U);
 #pragma unroll
     for (int q = 0; q < RB; q++) {
         Sp nb;
@@ -474,17 +488,17 @@ __device__ __forceinline__ void prefetch_hop(const K32 &a, unsigned ns, unsigned
     }
     if (!with_link) return;
     if (GF == GF_F32_12) {
-        const float4 *g = static_cast<const float4 *>(a.g) + (unsigned)mu * 3u * a.V;
+        const float4 *g = static_cast<const float4 *>(a.g) + (unsigned)mu * 3u * a.Vg;
 #pragma unroll
-        for (int c = 0; c < 3; c++) pf_l1(g + c * a.V + ls);
+        for (int c = 0; c < 3; c++) pf_l1(g + c * a.Vg + ls);
     } else if (GF == GF_F32_18) {
-        const float2 *g = static_cast<const float2 *>(a.g) + (unsigned)mu * 9u * a.V;
+        const float2 *g = static_cast<const float2 *>(a.g) + (unsigned)mu * 9u * a.Vg;
 #pragma unroll
-        for (int e = 0; e < 9; e++) pf_l1(g + e * a.V + ls);
+        for (int e = 0; e < 9; e++) pf_l1(g + e * a.Vg + ls);
     } else {
-        const uint2 *g = static_cast<const uint2 *>(a.g) + (unsigned)mu * 3u * a.V;
+        const uint2 *g = static_cast<const uint2 *>(a.g) + (unsigned)mu * 3u * a.Vg;
 #pragma unroll
-        for (int c = 0; c < 3; c++) pf_l1(g + c * a.V + ls);
+        for (int c = 0; c < 3; c++) pf_l1(g + c * a.Vg + ls);
     }
 }
 
@@ -514,23 +528,53 @@ __global__ void __launch_bounds__(TPB, MINB) k_dslash32(const K32 a) {
 #pragma unroll
     for (int q = 0; q < RB; q++) nrm[q] = 0.f;
     for (unsigned g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += gridDim.x * blockDim.x) {
-        const unsigned s = g >> kb_shift;
+        unsigned s = g >> kb_shift;  // output field index (traversal index when tiled)
         // a thread's RB RHS are KB apart, so every load instruction of a warp is contiguous
         const unsigned r0 = g & (KB - 1);
-        const unsigned q1 = fastdiv(s, a.d0), q2 = fastdiv(q1, a.d1), t = fastdiv(q2, a.d2);
-        const unsigned x = s - q1 * a.L0, y = q1 - q2 * a.L1, z = q2 - t * a.L2;
-        unsigned nbr[9], lks[8];
-        nbr[0] = x == a.L0 - 1 ? s - (a.L0 - 1) : s + 1;
-        nbr[1] = x == 0 ? s + (a.L0 - 1) : s - 1;
-        nbr[2] = y == a.L1 - 1 ? s - (a.L1 - 1) * s1 : s + s1;
-        nbr[3] = y == 0 ? s + (a.L1 - 1) * s1 : s - s1;
-        nbr[4] = z == a.L2 - 1 ? s - (a.L2 - 1) * s2 : s + s2;
-        nbr[5] = z == 0 ? s + (a.L2 - 1) * s2 : s - s2;
-        nbr[6] = t == a.L3 - 1 ? s - (a.L3 - 1) * s3 : s + s3;
-        nbr[7] = t == 0 ? s + (a.L3 - 1) * s3 : s - s3;
-        nbr[8] = s;
+        unsigned sl, x, y, z, t;  // lattice site and its coordinates
+        if (a.eo >= 0) {
+            // half-lattice index: the site of parity eo in x-pair s mod lh of row s / lh
+            const unsigned rest = a.lh > 1 ? fastdiv(s, a.dh) : s;
+            const unsigned q2 = fastdiv(rest, a.d1);
+            t = fastdiv(q2, a.d2);
+            y = rest - q2 * a.L1;
+            z = q2 - t * a.L2;
+            x = 2 * (s - rest * a.lh) + ((a.eo + y + z + t) & 1);
+            sl = x + rest * a.L0;
+        } else if (a.tile) {
+            const unsigned tb = a.tl0 + a.tl1 + a.tl2 + a.tl3;
+            const unsigned tid = s >> tb, w = s & ((1u << tb) - 1u);
+            const unsigned q1 = fastdiv(tid, a.dt0), q2 = fastdiv(q1, a.dt1), tt = fastdiv(q2, a.dt2);
+            x = ((tid - q1 * a.nt0) << a.tl0) + (w & ((1u << a.tl0) - 1u));
+            y = ((q1 - q2 * a.nt1) << a.tl1) + ((w >> a.tl0) & ((1u << a.tl1) - 1u));
+            z = ((q2 - tt * (a.L2 >> a.tl2)) << a.tl2) + ((w >> (a.tl0 + a.tl1)) & ((1u << a.tl2) - 1u));
+            t = (tt << a.tl3) + (w >> (a.tl0 + a.tl1 + a.tl2));
+            sl = x + a.L0 * (y + a.L1 * (z + a.L2 * t));
+            s = sl;
+        } else {
+            const unsigned q1 = fastdiv(s, a.d0), q2 = fastdiv(q1, a.d1);
+            t = fastdiv(q2, a.d2);
+            x = s - q1 * a.L0;
+            y = q1 - q2 * a.L1;
+            z = q2 - t * a.L2;
+            sl = s;
+        }
+        unsigned nbr[9], lks[8];  // neighbour sites (then field indices), link sites
+        nbr[0] = x == a.L0 - 1 ? sl - (a.L0 - 1) : sl + 1;
+        nbr[1] = x == 0 ? sl + (a.L0 - 1) : sl - 1;
+        nbr[2] = y == a.L1 - 1 ? sl - (a.L1 - 1) * s1 : sl + s1;
+        nbr[3] = y == 0 ? sl + (a.L1 - 1) * s1 : sl - s1;
+        nbr[4] = z == a.L2 - 1 ? sl - (a.L2 - 1) * s2 : sl + s2;
+        nbr[5] = z == 0 ? sl + (a.L2 - 1) * s2 : sl - s2;
+        nbr[6] = t == a.L3 - 1 ? sl - (a.L3 - 1) * s3 : sl + s3;
+        nbr[7] = t == 0 ? sl + (a.L3 - 1) * s3 : sl - s3;
 #pragma unroll
-        for (int h = 0; h < 8; h++) lks[h] = (h & 1) ? nbr[h] : s;
+        for (int h = 0; h < 8; h++) lks[h] = (h & 1) ? nbr[h] : sl;
+        if (a.eo >= 0) {
+#pragma unroll
+            for (int h = 0; h < 8; h++) nbr[h] >>= 1;  // the other parity's half-lattice field
+        }
+        nbr[8] = s;
         Sp acc[RB];
 #pragma unroll
         for (int q = 0; q < RB; q++)
@@ -559,7 +603,13 @@ __global__ void __launch_bounds__(TPB, MINB) k_dslash32(const K32 a) {
             hop_direct<3, SB, true, S, GF, RB>(a, nbr[7], lks[7], r0, KB, acc);
 #undef EIG_PF
 #pragma unroll
-            for (int q = 0; q < RB; q++) Store32<S>::load(a.in, a.in_s, a.P, s * a.k + r0 + q * KB, c0[q]);
+            for (int q = 0; q < RB; q++) {
+                if (a.eo < 0) Store32<S>::load(a.in, a.in_s, a.P, s * a.k + r0 + q * KB, c0[q]);
+                else if (a.cen) Store32<S>::load(a.cen, a.cen_s, a.P, s * a.k + r0 + q * KB, c0[q]);
+                else
+#pragma unroll
+                    for (int e = 0; e < 12; e++) c0[q].c[e] = f2(0.f, 0.f);  // hops only
+            }
         } else {
         // prologue: loads 0 .. NS-2
 #pragma unroll
@@ -587,7 +637,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_dslash32(const K32 a) {
         }
         cpa_wait<0>();
         }
-        const F2 d2 = f2(a.diag, a.diag), mh = f2(-0.5f, -0.5f);
+        const F2 d2 = f2(a.diag, a.diag), mh = f2(a.hcoef, a.hcoef);
 #pragma unroll
         for (int q = 0; q < RB; q++) {
             const unsigned rq = r0 + q * KB;

@@ -151,8 +151,13 @@ using namespace eig;
 
 struct eig_op_s {
     int L[4];
-    long V;
+    long V;        // lattice sites
+    long Vf;       // sites of a Krylov / basis field: V, or V / 2 for the odd-even form
+    bool eo = false;
+    FieldBuf tmp_e, tmp64_e;  // odd-even form: even-parity results of the first half stencil
+    FieldBuf full64, be64;    // odd-even form: full-lattice b / x, and b's even part
     double m_q;
+    unsigned long long gauge_hash = 0;  // fingerprint of the FP64 links (basis files)
     Prec prec;     // Krylov storage
     Prec wprec;    // window / basis / x_lo storage (P64 or P32)
     int gf_inner;
@@ -183,6 +188,11 @@ struct eig_op_s {
     std::vector<CgGraph> graphs;
     DevBuf tcerr;      // error flag of the tensor-core window restart
     PinBuf errh;
+    // spectrally preconditioned eigCG: z = P^{-1} r, G = shift H_p^{-1} - I, U_p^H r, G U_p^H r,
+    // tensor-core partial sums and error flags
+    FieldBuf zsp;
+    DevBuf spG, spC, spY, sptc, sperr;
+    PinBuf sperrh;
     DevBuf jbase_dev;  // iteration base the replayed kernels add to their offsets
     PinBuf jbase_h;
     cudaStream_t cap_stream = nullptr;  // private stream the graphs are captured on
@@ -192,8 +202,8 @@ struct eig_op_s {
         if (cap_stream) cudaStreamDestroy(cap_stream);
     }
 
-    long ncomplex() const { return V * 12; }
-    size_t wfield_bytes() const { return field_bytes(wprec, V, 1); }
+    long ncomplex() const { return Vf * 12; }
+    size_t wfield_bytes() const { return field_bytes(wprec, Vf, 1); }
     RedScratch red() const {
         RedScratch r;
         r.partials = red_partials.as<double>();
@@ -220,6 +230,7 @@ struct eig_op_s {
         c.k = in.v.k;
         c.diag = 4.0 + m_q;
         c.dagger = dag;
+        c.cen = Field{};
         return c;
     }
     History history(int k) const {
@@ -260,7 +271,7 @@ struct eig_basis_s {
     DevBuf tcpart, tcerr;   // partial sums and error flag of the tensor-core U^H R
     PinBuf Ch, errh;
     std::mutex mu;
-    long fsize() const { return op->V * 12; }  // complex entries per field
+    long fsize() const { return op->Vf * 12; }  // complex entries per field
 };
 
 namespace eig {
@@ -291,8 +302,30 @@ static void zero_field(Field f, cudaStream_t s) {
 // ------------------------------------------------------------------------------------
 // building blocks on an op
 // ------------------------------------------------------------------------------------
+// The call that applies M (dag: M^H) to in.  For an odd-even operator the matrix is
+// M_hat = d - (1/d) H_oe H_eo on the odd sites (d = 4 + m_q, H the hopping part of M):
+// this launches the first half stencil, tmp_e = H_eo in (or (H^H)_eo in), and returns
+// the second, out = d in + (1/2d) (hop sum of tmp_e), which the caller launches with
+// the epilogue it needs.
+static DslashCall mcall(eig_op_s *op, Field in, Field out, bool dag, bool f64, cudaStream_t s) {
+    DslashCall c = op->call(in, out, dag, f64);
+    if (!op->eo) return c;
+    Field tmp = (f64 ? op->tmp64_e : op->tmp_e).view(in.v.k);
+    DslashCall c1 = c;
+    c1.out = tmp;
+    c1.eo_parity = 0;
+    c1.diag = 0.0;
+    c1.hcoef = -0.5;
+    CUDA_CK(launch_dslash(c1, s));
+    c.in = tmp;
+    c.cen = in;
+    c.eo_parity = 1;
+    c.hcoef = 0.5 / c.diag;
+    return c;
+}
+
 static void apply_M(eig_op_s *op, Field in, Field out, bool dag, bool f64, cudaStream_t s) {
-    CUDA_CK(launch_dslash(op->call(in, out, dag, f64), s));
+    CUDA_CK(launch_dslash(mcall(op, in, out, dag, f64, s), s));
 }
 
 // out = A in in FP64 (uses op->u64 as scratch; in/out must not be u64)
@@ -304,7 +337,7 @@ static void apply_A64(eig_op_s *op, Field in, Field out, cudaStream_t s) {
 
 // natural (host or device) -> internal FP64 field
 static void load_natural(eig_op_s *op, const double *nat, Field dst, cudaStream_t s) {
-    const size_t bytes = (size_t)op->V * 12 * 16 * dst.v.k;
+    const size_t bytes = (size_t)dst.v.V * 12 * 16 * dst.v.k;
     const double *src = nat;
     if (!is_device_ptr(nat)) {
         CUDA_CK(cudaMemcpyAsync(op->nat_in.p, nat, bytes, cudaMemcpyHostToDevice, s));
@@ -314,13 +347,62 @@ static void load_natural(eig_op_s *op, const double *nat, Field dst, cudaStream_
 }
 
 static void store_natural(eig_op_s *op, Field src, double *nat, cudaStream_t s) {
-    const size_t bytes = (size_t)op->V * 12 * 16 * src.v.k;
+    const size_t bytes = (size_t)src.v.V * 12 * 16 * src.v.k;
     if (is_device_ptr(nat)) {
         CUDA_CK(launch_unpack(src, nat, s));
     } else {
         CUDA_CK(launch_unpack(src, op->nat_out.as<double>(), s));
         CUDA_CK(cudaMemcpyAsync(nat, op->nat_out.p, bytes, cudaMemcpyDeviceToHost, s));
     }
+}
+
+// Loads b and the initial guess x (k RHS) of a solve.  Full-lattice operators: into
+// b64 / x64.  Odd-even operators: b and x are full-lattice vectors of M x = b; b64
+// receives M_hat^H b_hat with b_hat = b_o - (1/d) H_oe b_e, the right-hand side of the
+// odd-site normal equations, x64 the odd part of x, and op->be64 keeps b_e.
+static void load_solve(eig_op_s *op, const double *b, const double *x, Field b64, Field x64, cudaStream_t s) {
+    if (!op->eo) {
+        load_natural(op, b, b64, s);
+        load_natural(op, x, x64, s);
+        return;
+    }
+    const int k = b64.v.k;
+    Field full = op->full64.view(k), be = op->be64.view(k), u = op->u64.view(k);
+    const double d = 4.0 + op->m_q;
+    load_natural(op, b, full, s);
+    CUDA_CK(launch_parity_move(full, be, 0, op->L, true, s));
+    CUDA_CK(launch_parity_move(full, b64, 1, op->L, true, s));
+    DslashCall c = op->call(be, u, false, true);  // u = H_oe b_e
+    c.eo_parity = 1;
+    c.diag = 0.0;
+    c.hcoef = -0.5;
+    CUDA_CK(launch_dslash(c, s));
+    CUDA_CK(launch_combine(b64, 1.0, b64, -1.0 / d, u, s));  // b_hat
+    apply_M(op, b64, u, true, true, s);                        // M_hat^H b_hat
+    CUDA_CK(launch_combine(b64, 1.0, u, 0.0, null_field(), s));
+    load_natural(op, x, full, s);
+    CUDA_CK(launch_parity_move(full, x64, 1, op->L, true, s));
+}
+
+// Stores a solve's solution.  Odd-even operators: x_e = (b_e - H_eo x_o) / d, then the
+// full-lattice x from x_e and x_o.
+static void store_solve(eig_op_s *op, Field x64, double *x, cudaStream_t s) {
+    if (!op->eo) {
+        store_natural(op, x64, x, s);
+        return;
+    }
+    const int k = x64.v.k;
+    Field full = op->full64.view(k), be = op->be64.view(k), t = op->tmp64_e.view(k);
+    const double d = 4.0 + op->m_q;
+    DslashCall c = op->call(x64, t, false, true);  // t = H_eo x_o
+    c.eo_parity = 0;
+    c.diag = 0.0;
+    c.hcoef = -0.5;
+    CUDA_CK(launch_dslash(c, s));
+    CUDA_CK(launch_combine(be, 1.0 / d, be, -1.0 / d, t, s));
+    CUDA_CK(launch_parity_move(full, be, 0, op->L, false, s));
+    CUDA_CK(launch_parity_move(full, x64, 1, op->L, false, s));
+    store_natural(op, full, x, s);
 }
 
 // ------------------------------------------------------------------------------------
@@ -383,6 +465,11 @@ struct Solve {
     int j = 0;                  // last issued iteration
     int j_checked = 0;          // history read up to here
     double tol;
+    // spectral preconditioner from the first spl vectors of spB (Sec. 2): z = P^{-1} r
+    bool sp = false;
+    Field z;
+    eig_basis_s *spB = nullptr;
+    int spl = 0;
 
     void read_scalars() {
         CUDA_CK(cudaMemcpyAsync(sth, st, sizeof(CGScalars) * k, cudaMemcpyDeviceToHost, s));
@@ -410,17 +497,40 @@ struct Solve {
             CUDA_CK(launch_combine(x64, 1.0, x64, 1.0, xlo, s));
             zero_field(xlo, s);
         }
-        if (mixed && !final_check) {
-            const long n = op->V * 12 * (long)k;
+        if (mixed && !final_check && !op->eo) {
+            const long n = op->Vf * 12 * (long)k;
             CUDA_CK(launch_to_dd(x64.v.data, r64.v.data, n, s));  // r64 holds x in dd until overwritten
             CUDA_CK(launch_dslash_dd(op->call(x64, u64, false, true), op->gauge_dd.p, r64.v.data, u64.v.data, s));
             CUDA_CK(launch_dslash_dd_resid(op->call(u64, r64, true, true), op->gauge_dd.p, u64.v.data, b64, r64, st, h,
                                            j, set_rho, red, s));
         } else {
             apply_M(op, x64, u64, false, true, s);
-            CUDA_CK(launch_dslash_resid(op->call(u64, r64, true, true), b64, r64, st, h, j, set_rho, red, s));
+            CUDA_CK(launch_dslash_resid(mcall(op, u64, r64, true, true, s), b64, r64, st, h, j, set_rho, red, s));
         }
         if (mixed && set_rho) CUDA_CK(launch_combine(r, 1.0, r64, 0.0, null_field(), s));
+    }
+
+    // r64 = b64 - A x64 for the deflation of the initial guess (Eq. 1): r64 = b64 when
+    // every x is zero, else the double-float stencil in mixed precision (full lattice)
+    // or the FP64 one.
+    void initial_residual() {
+        CUDA_CK(launch_norm2(x64, st, false, h, 0, red, s));
+        read_scalars();
+        bool zero = true;
+        for (int q = 0; q < k; q++) zero = zero && sth[q].aux == 0.0;
+        if (zero) {
+            CUDA_CK(launch_combine(r64, 1.0, b64, 0.0, null_field(), s));
+        } else if (mixed && !op->eo) {
+            const long n = op->Vf * 12 * (long)k;
+            CUDA_CK(launch_to_dd(x64.v.data, r64.v.data, n, s));  // r64 holds x in dd until overwritten
+            CUDA_CK(launch_dslash_dd(op->call(x64, u64, false, true), op->gauge_dd.p, r64.v.data, u64.v.data, s));
+            CUDA_CK(launch_dslash_dd_resid(op->call(u64, r64, true, true), op->gauge_dd.p, u64.v.data, b64, r64, st, h,
+                                           0, false, red, s));
+        } else {
+            apply_M(op, x64, u64, false, true, s);
+            apply_M(op, u64, r64, true, true, s);
+            CUDA_CK(launch_combine(r64, 1.0, b64, -1.0, r64, s));
+        }
     }
 
     // Sets up r, rho, target from b64 and the initial guess in x64.
@@ -517,9 +627,9 @@ static cudaGraphExec_t cg_graph(Solve &sv, eig_op_s *op) {
     for (int t = 1; t <= CHECK && e == cudaSuccess; t++) {
         e = launch_pupdate(sv.r, sv.p, sv.xlo, false, sv.st, null_field(), s);
         if (e == cudaSuccess)
-            e = launch_dslash_norm(op->call(sv.p, sv.u, false, op->prec == P64), sv.st, hg, t, sv.red, s);
+            e = launch_dslash_norm(mcall(op, sv.p, sv.u, false, op->prec == P64, s), sv.st, hg, t, sv.red, s);
         if (e == cudaSuccess)
-            e = launch_dslash_cg(op->call(sv.u, sv.u, true, op->prec == P64), sv.r, null_field(), sv.st, hg, t,
+            e = launch_dslash_cg(mcall(op, sv.u, sv.u, true, op->prec == P64, s), sv.r, null_field(), sv.st, hg, t,
                                  sv.red, s);
     }
     prof_record_end();
@@ -542,6 +652,34 @@ static cudaGraphExec_t cg_graph(Solve &sv, eig_op_s *op) {
     }
     op->graphs.push_back(std::move(gr));
     return op->graphs.back().exec;
+}
+
+static ColSet basis_cols(eig_basis_s *B, int first, int n);
+
+// z = P^{-1} r = r + U_p (G (U_p^H r)) with the spectral preconditioner of the first spl
+// basis vectors, then rho = r^H z and beta_j (Fig. 1 steps 3-4 and 8 in preconditioned
+// form; iter = the last finished iteration).  No host synchronisation: the contractions'
+// error flags are checked when the solve ends.
+static void sp_apply(Solve &sv, int iter) {
+    eig_op_s *op = sv.op;
+    eig_basis_s *B = sv.spB;
+    cudaStream_t s = sv.s;
+    const bool f64 = op->wprec == P64;
+    const long nrow = op->ncomplex();
+    const ColSet U = basis_cols(B, 0, sv.spl);
+    const ColSet R = field_cols(sv.r.v.data, f64, 1, nrow, 1, true);
+    if (tc_gemm_enabled() && tc_ahb_ok(U, R))
+        CUDA_CK(launch_tc_ahb(U, R, nrow, op->spC.as<double>(), op->sptc.as<double>(), op->sperr.as<int>(), s));
+    else
+        CUDA_CK(launch_gemm_ahb(U, R, nrow, op->spC.as<double>(), sv.red, s));
+    CUDA_CK(launch_sp_coef(op->spG.as<double>(), op->spC.as<double>(), op->spY.as<double>(), sv.spl, s));
+    CUDA_CK(launch_combine(sv.z, 1.0, sv.r, 0.0, null_field(), s));
+    const ColSet Z = field_cols(sv.z.v.data, f64, 1, nrow, 1, true);
+    if (tc_gemm_enabled() && (nrow % 2) == 0 && tc_ay_ok(U, Z))
+        CUDA_CK(launch_tc_ay(U, op->spY.as<double>(), Z, 1.0, nrow, op->sperr.as<int>() + 1, s));
+    else
+        CUDA_CK(launch_gemm_ay(U, op->spY.as<double>(), Z, 1.0, nrow, s));
+    CUDA_CK(launch_pcg_rho(sv.r, sv.z, sv.st, sv.h, iter, sv.red, s));
 }
 
 // Runs CG iterations until every RHS is inactive or max_iter.  With a window,
@@ -576,7 +714,7 @@ static bool cg_run(Solve &sv, int max_iter, Window *w, eig_op_s *op) {
             sv.j_checked = sv.j;
             since = 0;
         }
-        if (!w && since == 0 && sv.j >= 1 && sv.j + CHECK <= max_iter && cg_graphs_enabled()) {
+        if (!w && !sv.sp && since == 0 && sv.j >= 1 && sv.j + CHECK <= max_iter && cg_graphs_enabled()) {
             // CHECK plain iterations as one replayed CUDA graph
             cudaGraphExec_t g = cg_graph(sv, op);
             *op->jbase_h.as<int>() = sv.j;
@@ -610,26 +748,27 @@ static bool cg_run(Solve &sv, int max_iter, Window *w, eig_op_s *op) {
                 slot = w->freel.back();
             }
             w->freel.pop_back();
-            vapp = field_at(op->wprec, (char *)op->win.p + (size_t)slot * op->wfield_bytes(), op->V, 1);
+            vapp = field_at(op->wprec, (char *)op->win.p + (size_t)slot * op->wfield_bytes(), op->Vf, 1);
         }
-        CUDA_CK(launch_pupdate(sv.r, sv.p, sv.xlo, j == 1, sv.st, vapp, s));
-        CUDA_CK(launch_dslash_norm(op->call(sv.p, sv.u, false, op->prec == P64),
-                                   sv.st, sv.h, j, sv.red, s));
+        if (sv.sp) sp_apply(sv, j - 1);  // Fig. 1 steps 3-4 and 8 with P != I
+        CUDA_CK(launch_pupdate(sv.sp ? sv.z : sv.r, sv.p, sv.xlo, j == 1, sv.st, vapp, s));
+        CUDA_CK(launch_dslash_norm(mcall(op, sv.p, sv.u, false, op->prec == P64, s), sv.st, sv.h, j, sv.red, s));
         Field tsave = null_field();
         if (w) {
             const bool becomes_full = !restart_now && (w->i + 1 == w->m);
             void *tp = w->tprev_is_a ? op->tprev.p : op->tcur.p;
             void *tc = w->tprev_is_a ? op->tcur.p : op->tprev.p;
-            if (restart_now) tsave = field_at(op->wprec, tc, op->V, 1);
-            else if (becomes_full) tsave = field_at(op->wprec, tp, op->V, 1);
+            if (restart_now) tsave = field_at(op->wprec, tc, op->Vf, 1);
+            else if (becomes_full) tsave = field_at(op->wprec, tp, op->Vf, 1);
         }
-        CUDA_CK(launch_dslash_cg(op->call(sv.u, sv.u, true, op->prec == P64), sv.r, tsave, sv.st, sv.h, j, sv.red, s));
+        CUDA_CK(launch_dslash_cg(mcall(op, sv.u, sv.u, true, op->prec == P64, s), sv.r, tsave, sv.st, sv.h, j, sv.red,
+                                 s));
         if (w) {
             if (restart_now) {
                 // step 11.7 (V <- V QZ in place) fused with step 11.8 (w^H V)
                 const int m = w->m;
                 std::vector<long> off(m);
-                const long fs = (long)op->V * 12;
+                const long fs = (long)op->Vf * 12;
                 for (int a = 0; a < m; a++) off[a] = (long)w->slots[a] * fs;
                 CUDA_CK(cudaMemcpyAsync(op->col_off.p, off.data(), m * sizeof(long), cudaMemcpyHostToDevice, s));
                 std::vector<double> qz((size_t)m * nout * 2);
@@ -652,17 +791,15 @@ static bool cg_run(Solve &sv, int max_iter, Window *w, eig_op_s *op) {
                 if (tcw) {
                     // V <- V QZ on the tensor cores, in place (each CTA reads all m columns of
                     // its rows before writing them), then w^H V_new with w = t - beta t_prev
+                    // formed on the fly
                     ColSet Out = Vw;
                     Out.ncols = nout;
                     op->tcerr.ensure(16);
                     op->errh.ensure(16);
                     CUDA_CK(cudaMemsetAsync(op->tcerr.p, 0, 16, s));
                     CUDA_CK(launch_tc_ay(Vw, op->qz.as<double>(), Out, 0.0, op->ncomplex(), op->tcerr.as<int>(), s));
-                    Field wf = op->rsv.view(1);
-                    CUDA_CK(launch_w_diff(tc, tp, sv.h.beta + (size_t)j * k, wf.v.data, op->ncomplex(), s));
-                    // V_new^H w (nout x 1), conjugated below to w^H V_new
-                    ColSet W1 = field_cols(wf.v.data, false, 1, op->V * 12, 1, false);
-                    CUDA_CK(launch_gemm_ahb(Out, W1, op->ncomplex(), op->wv.as<double>(), sv.red, s));
+                    CUDA_CK(launch_wdot(tc, tp, sv.h.beta + (size_t)j * k, op->win.p, op->col_off.as<long>(), nout,
+                                        op->ncomplex(), op->wv.as<double>(), sv.red, s));
                     CUDA_CK(cudaMemcpyAsync(op->errh.p, op->tcerr.p, 4, cudaMemcpyDeviceToHost, s));
                 } else {
                     CUDA_CK(launch_window_restart(Vw, m, op->qz.as<double>(), nout, tc, tp, sv.h.beta + (size_t)j * k,
@@ -674,8 +811,6 @@ static bool cg_run(Solve &sv, int max_iter, Window *w, eig_op_s *op) {
                     throw Error{EIG_ERR_TIMEOUT, "tensor-core window restart: a bounded wait in the kernel gave up"};
                 std::vector<double> wv(2 * nout);
                 CUDA_CK(cudaMemcpy(wv.data(), op->wv.p, wv.size() * sizeof(double), cudaMemcpyDeviceToHost));
-                if (tcw)
-                    for (int c = 0; c < nout; c++) wv[2 * c + 1] = -wv[2 * c + 1];
                 std::vector<int> newslots(w->slots.begin(), w->slots.begin() + nout);
                 for (int a = nout; a < m; a++) w->freel.push_back(w->slots[a]);
                 newslots.push_back(slot);
@@ -728,6 +863,11 @@ static void tune_for(eig_op_s *op, int k, cudaStream_t s) {
     DslashCall c = op->call(op->p.view(k), op->u.view(k), false, false);
     c.gauge.data = op->gauge_in.p;
     c.gformat = op->gf_inner;
+    if (op->eo) {  // the half stencil of the odd-even form, on half-lattice fields
+        c.eo_parity = 1;
+        c.cen = op->r.view(k);
+        c.hcoef = 0.5 / c.diag;
+    }
     const void *alts[1] = {op->gauge_alt.p};
     const int gfs[1] = {op->gf_alt};
     CUDA_CK(autotune_dslash32(c, alts, gfs, 1, s));
@@ -903,6 +1043,52 @@ static void deflate_into(eig_basis_s *B, Field r64, Field x64, cudaStream_t s) {
 
 }  // namespace eig
 
+// ------------------------------------------------------------------------------------
+// basis files
+// ------------------------------------------------------------------------------------
+namespace eig {
+
+// FNV-1a mixing (xor, multiply by the 64-bit FNV prime) applied per 64-bit word of the
+// FP64 links: identifies the gauge field a saved basis belongs to.
+static unsigned long long links_fingerprint(const double *g, size_t n) {
+    unsigned long long h = 0xcbf29ce484222325ull;
+    for (size_t i = 0; i < n; i++) {
+        unsigned long long w;
+        memcpy(&w, g + i, sizeof w);
+        h = (h ^ w) * 0x100000001b3ull;
+    }
+    return h;
+}
+
+// 64-byte header of a basis file; then H (l x l complex FP64, row-major) and the l
+// vectors in natural layout (fsize complex entries each, real_bytes per real).
+struct BasisFileHeader {
+    char magic[8];
+    int32_t version;
+    int32_t dims[4];
+    int32_t even_odd;
+    int32_t real_bytes;
+    int32_t l;
+    int64_t fsize;
+    double m_q;
+    unsigned long long gauge_hash;
+};
+static_assert(sizeof(BasisFileHeader) == 64, "basis file header layout");
+static const char BASIS_MAGIC[8] = {'E', 'I', 'G', 'B', 'A', 'S', 'I', 'S'};
+
+struct File {
+    FILE *f = nullptr;
+    ~File() {
+        if (f) fclose(f);
+    }
+};
+
+static void io_check(bool ok, const std::string &what) {
+    if (!ok) throw Error{EIG_ERR_IO, what};
+}
+
+}  // namespace eig
+
 // ======================================================================================
 // C ABI
 // ======================================================================================
@@ -966,7 +1152,11 @@ eig_status eig_op_create(const double *gauge, const int dims[4], double m_q, con
         o.link_compress12 = 1;
         o.max_rhs = 1;
         o.reliable_delta = 0.1;
+        o.even_odd = 0;
     }
+    ARG_CHECK(o.even_odd == 0 || o.even_odd == 1, "even_odd must be 0 or 1");
+    if (o.even_odd)
+        for (int i = 0; i < 4; i++) ARG_CHECK(dims[i] % 2 == 0, "the odd-even form needs every lattice extent even");
     ARG_CHECK(o.spinor_prec == 64 || o.spinor_prec == 32 || o.spinor_prec == 16, "spinor_prec must be 64, 32 or 16");
     ARG_CHECK(o.max_rhs >= 1 && o.max_rhs <= MAX_RHS && (o.max_rhs & (o.max_rhs - 1)) == 0,
               "max_rhs must be a power of two in [1, 16]");
@@ -976,6 +1166,8 @@ eig_status eig_op_create(const double *gauge, const int dims[4], double m_q, con
     std::unique_ptr<eig_op_s> op(new eig_op_s());
     for (int i = 0; i < 4; i++) op->L[i] = dims[i];
     op->V = V;
+    op->eo = o.even_odd == 1;
+    op->Vf = op->eo ? V / 2 : V;
     op->m_q = m_q;
     op->prec = o.spinor_prec == 64 ? P64 : (o.spinor_prec == 32 ? P32 : P16);
     op->wprec = op->prec == P64 ? P64 : P32;
@@ -983,6 +1175,7 @@ eig_status eig_op_create(const double *gauge, const int dims[4], double m_q, con
     op->max_rhs = o.max_rhs;
     op->delta = (o.reliable_delta > 0.0 && o.reliable_delta < 1.0) ? o.reliable_delta : 0.1;
     const int K = o.max_rhs;
+    op->gauge_hash = links_fingerprint(gauge, (size_t)V * 4 * 9 * 2);
     // gauge: host -> device staging -> packed formats
     eig::DevBuf stage;
     stage.alloc((size_t)V * 4 * 9 * 16);
@@ -1004,19 +1197,26 @@ eig_status eig_op_create(const double *gauge, const int dims[4], double m_q, con
         }
     }
     CUDA_CK(cudaDeviceSynchronize());
-    // workspace
-    op->r.alloc(op->prec, V, K);
-    op->p.alloc(op->prec, V, K);
-    op->u.alloc(op->prec, V, K);
-    op->b64.alloc(P64, V, K);
-    op->x64.alloc(P64, V, K);
-    op->u64.alloc(P64, V, K);
+    // workspace (fields of Vf sites: half-lattice fields for the odd-even form)
+    const long Vf = op->Vf;
+    op->r.alloc(op->prec, Vf, K);
+    op->p.alloc(op->prec, Vf, K);
+    op->u.alloc(op->prec, Vf, K);
+    op->b64.alloc(P64, Vf, K);
+    op->x64.alloc(P64, Vf, K);
+    op->u64.alloc(P64, Vf, K);
     if (op->prec != P64) {
-        op->xlo.alloc(P32, V, K);
-        op->r64.alloc(P64, V, K);
+        op->xlo.alloc(P32, Vf, K);
+        op->r64.alloc(P64, Vf, K);
     }
-    op->rsv.alloc(op->wprec, V, K);
-    op->xsv.alloc(op->wprec, V, K);
+    op->rsv.alloc(op->wprec, Vf, K);
+    op->xsv.alloc(op->wprec, Vf, K);
+    if (op->eo) {
+        op->tmp_e.alloc(op->prec, Vf, K);
+        op->tmp64_e.alloc(P64, Vf, K);
+        op->full64.alloc(P64, V, K);
+        op->be64.alloc(P64, Vf, K);
+    }
     op->nat_in.alloc((size_t)V * 12 * 16 * K);
     op->nat_out.alloc((size_t)V * 12 * 16 * K);
     op->st.alloc(sizeof(CGScalars) * MAX_RHS);
@@ -1043,13 +1243,14 @@ eig_status eig_op_apply(eig_op op, int which, const double *in, double *out, int
     ARG_CHECK(op && in && out, "null argument");
     ARG_CHECK(which >= 0 && which <= 3, "which must be 0 (M), 1 (M^H), 2 (A) or 3 (A in double-float)");
     ARG_CHECK(which != 3 || op->prec != P64, "which = 3 needs an FP32 or FP16 op");
+    ARG_CHECK(which != 3 || !op->eo, "which = 3 is not available for odd-even operators");
     ARG_CHECK(k >= 1 && k <= op->max_rhs && (k & (k - 1)) == 0, "k must be a power of two <= max_rhs");
     std::lock_guard<std::mutex> lk(op->mu);
     cudaStream_t s = (cudaStream_t)stream;
     Field x64 = op->x64.view(k);
     load_natural(op, in, x64, s);
     if (which == 3) {  // A = M^H M in double-float arithmetic
-        const long n = op->V * 12 * (long)k;
+        const long n = op->Vf * 12 * (long)k;
         Field t1 = op->u64.view(k), t2 = op->r64.view(k);
         CUDA_CK(launch_to_dd(x64.v.data, t1.v.data, n, s));
         CUDA_CK(launch_dslash_dd(op->call(x64, t2, false, true), op->gauge_dd.p, t1.v.data, t2.v.data, s));
@@ -1071,6 +1272,27 @@ eig_status eig_op_apply(eig_op op, int which, const double *in, double *out, int
     CUDA_CK(launch_combine(x64, 1.0, b, 0.0, null_field(), s));
     store_natural(op, x64, out, s);
     sync(s);
+    API_END
+}
+
+eig_status eig_op_stencil_choice(eig_op op, int k, int *variant, int *link_reals) {
+    API_BEGIN
+    ARG_CHECK(op && variant && link_reals, "null argument");
+    ARG_CHECK(k >= 1 && k <= op->max_rhs && (k & (k - 1)) == 0, "k must be a power of two <= max_rhs");
+    *variant = -1;
+    *link_reals = 0;
+    if (op->prec == P64) return EIG_OK;
+    // the call tune_for times: the primary link format, half stencil for odd-even ops
+    DslashCall c = op->call(op->p.view(k), op->u.view(k), false, false);
+    c.gauge.data = op->gauge_in.p;
+    c.gformat = op->gf_inner;
+    if (op->eo) {
+        c.eo_parity = 1;
+        c.cen = op->r.view(k);
+        c.hcoef = 0.5 / c.diag;
+    }
+    const int gf = dslash32_choice(c, variant);
+    *link_reals = gf < 0 ? 0 : (gf == GF_F32_12 || gf == GF_F16_12 ? 12 : 18);
     API_END
 }
 
@@ -1121,10 +1343,17 @@ eig_status eig_basis_truncate(eig_basis basis, int l) {
     API_END
 }
 
-eig_status eig_eigcg_solve(eig_op op, eig_basis basis, const double *b, double *x, int nev, int m, double tol,
-                           int max_iter, eig_stats *stats, void *stream) {
+// eigCG (Fig. 1) on one RHS; with sp_vecs > 0 preconditioned by the spectral
+// preconditioner of the basis' first sp_vecs vectors (Sec. 2): P^{-1} = (I - U_p U_p^H) +
+// sp_shift U_p H_p^{-1} U_p^H, applied as r + U_p (sp_shift H_p^{-1} - I) U_p^H r.
+static eig_status eigcg_impl(eig_op op, eig_basis basis, const double *b, double *x, int nev, int m, double tol,
+                             int max_iter, int sp_vecs, double sp_shift, eig_stats *stats, void *stream) {
     API_BEGIN
     ARG_CHECK(op && b && x, "null argument");
+    ARG_CHECK(sp_vecs == 0 || (basis && sp_vecs >= 1 && sp_vecs <= basis->l),
+              "sp_vecs must be 0 or in [1, basis size]");
+    ARG_CHECK(sp_vecs == 0 || (std::isfinite(sp_shift) && sp_shift > 0.0), "sp_shift must be positive");
+    ARG_CHECK(sp_vecs == 0 || op->prec != P16, "spectral preconditioning needs an FP64 or FP32 op");
     ARG_CHECK(nev >= 1 && nev <= MAX_NEV, "nev must be in [1, 16]");
     ARG_CHECK(m > 2 * nev && m <= MAX_WINDOW, "need 2*nev < m <= 128");
     ARG_CHECK(tol > 0.0 && tol < 1.0, "tol must be in (0, 1)");
@@ -1145,15 +1374,44 @@ eig_status eig_eigcg_solve(eig_op op, eig_basis basis, const double *b, double *
     op->qz.ensure((size_t)MAX_WINDOW * 2 * MAX_NEV * 16);
     op->wv.ensure(2 * MAX_NEV * 16);
     Solve sv = make_solve(op, 1, s, max_iter);
-    load_natural(op, b, sv.b64, s);
-    load_natural(op, x, sv.x64, s);
+    load_solve(op, b, x, sv.b64, sv.x64, s);
     if (basis && basis->l > 0) {
         // init-CG part of the Sec. 4 box: x0 = x~0 + U H^{-1} U^H (b - A x~0)
-        apply_A64(op, sv.x64, sv.r64, s);
-        CUDA_CK(launch_combine(sv.r64, 1.0, sv.b64, -1.0, sv.r64, s));
+        sv.initial_residual();
         deflate_into(basis, sv.r64, sv.x64, s);
     }
     sv.start(tol);
+    if (sp_vecs > 0) {
+        // G = shift H_p^{-1} - I from the leading sp_vecs x sp_vecs block of H
+        const int lp = sp_vecs, l = basis->l;
+        std::vector<cd> L((size_t)lp * lp), Inv((size_t)lp * lp, cd(0.0));
+        for (int a = 0; a < lp; a++)
+            for (int c = 0; c < lp; c++) L[(size_t)a * lp + c] = basis->H[(size_t)a * l + c];
+        if (!dense::cholesky(lp, L.data())) throw Error{EIG_ERR_BREAKDOWN, "leading block of H is not positive definite"};
+        for (int a = 0; a < lp; a++) Inv[(size_t)a * lp + a] = 1.0;
+        dense::chol_solve(lp, L.data(), Inv.data(), lp);  // column q: H_p^{-1} e_q
+        std::vector<double> G((size_t)lp * lp * 2);
+        for (int a = 0; a < lp; a++)
+            for (int c = 0; c < lp; c++) {
+                const cd g = sp_shift * Inv[(size_t)c * lp + a] - (a == c ? 1.0 : 0.0);
+                G[((size_t)a * lp + c) * 2] = g.real();
+                G[((size_t)a * lp + c) * 2 + 1] = g.imag();
+            }
+        op->spG.ensure(G.size() * sizeof(double));
+        CUDA_CK(cudaMemcpyAsync(op->spG.p, G.data(), G.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+        if (op->zsp.kcap < 1) op->zsp.alloc(op->prec, op->Vf, 1);
+        op->spC.ensure((size_t)lp * 16);
+        op->spY.ensure((size_t)lp * 16);
+        op->sptc.ensure(tc_ahb_partials_bytes(op->ncomplex(), lp, 1));
+        op->sperr.ensure(16);
+        op->sperrh.ensure(16);
+        CUDA_CK(cudaMemsetAsync(op->sperr.p, 0, 16, s));
+        sync(s);  // G must outlive the async copy
+        sv.sp = true;
+        sv.z = op->zsp.view(1);
+        sv.spB = basis;
+        sv.spl = lp;
+    }
     Window w;
     w.nev = nev;
     w.m = m;
@@ -1168,6 +1426,12 @@ eig_status eig_eigcg_solve(eig_op op, eig_basis basis, const double *b, double *
             break;
         }
         if (!cg_finish(sv, max_iter, &w, op, rounds)) break;
+    }
+    if (sv.sp) {
+        CUDA_CK(cudaMemcpyAsync(op->sperrh.p, op->sperr.p, 8, cudaMemcpyDeviceToHost, s));
+        sync(s);
+        if (op->sperrh.as<int>()[0] != 0 || op->sperrh.as<int>()[1] != 0)
+            throw Error{EIG_ERR_TIMEOUT, "spectral preconditioner: a bounded wait in a tensor-core kernel gave up"};
     }
     // eigCG output: nev lowest Ritz pairs of the final window
     int nr = 0;
@@ -1209,7 +1473,7 @@ eig_status eig_eigcg_solve(eig_op op, eig_basis basis, const double *b, double *
     } else if (basis) {
         basis->npend = 0;
     }
-    store_natural(op, sv.x64, x, s);
+    store_solve(op, sv.x64, x, s);
     sync(s);
     if (stats) {
         stats->iters = J;
@@ -1228,6 +1492,20 @@ eig_status eig_eigcg_solve(eig_op op, eig_basis basis, const double *b, double *
         return EIG_NOT_CONVERGED;
     }
     API_END
+}
+
+eig_status eig_eigcg_solve(eig_op op, eig_basis basis, const double *b, double *x, int nev, int m, double tol,
+                           int max_iter, eig_stats *stats, void *stream) {
+    return eigcg_impl(op, basis, b, x, nev, m, tol, max_iter, 0, 0.0, stats, stream);
+}
+
+eig_status eig_eigcg_solve_sp(eig_op op, eig_basis basis, const double *b, double *x, int nev, int m, double tol,
+                              int max_iter, int sp_vecs, double sp_shift, eig_stats *stats, void *stream) {
+    if (sp_vecs < 1) {
+        eig::g_last_error = "sp_vecs must be >= 1 (eig_eigcg_solve solves without a preconditioner)";
+        return EIG_ERR_ARG;
+    }
+    return eigcg_impl(op, basis, b, x, nev, m, tol, max_iter, sp_vecs, sp_shift, stats, stream);
 }
 
 eig_status eig_basis_grow(eig_basis B, void *stream) {
@@ -1299,26 +1577,26 @@ eig_status eig_basis_grow(eig_basis B, void *stream) {
                                 (size_t)r * op->wfield_bytes(), cudaMemcpyDeviceToDevice, s));
         sync(s);
     }
-    if (op->prec != P64) {
+    if (op->prec != P64 && !op->eo) {
         // W = A V-bar in double-float arithmetic (about 44 bits, far below the FP32
         // rounding of the stored W), up to max_rhs columns per stencil launch
         const long cstride = (long)(op->wfield_bytes() / 16);
         for (int c0 = 0; c0 < r; c0 += op->max_rhs) {
             const int n = std::min(op->max_rhs, r - c0);
             Field xin = op->r64.view(n), mid = op->u64.view(n), wout = op->x64.view(n);
-            CUDA_CK(launch_cols32_to_dd((char *)B->U.p + (size_t)(l + c0) * op->wfield_bytes(), cstride, op->V, n,
+            CUDA_CK(launch_cols32_to_dd((char *)B->U.p + (size_t)(l + c0) * op->wfield_bytes(), cstride, op->Vf, n,
                                         xin.v.data, s));
             CUDA_CK(launch_dslash_dd(op->call(xin, mid, false, true), op->gauge_dd.p, xin.v.data, mid.v.data, s));
             CUDA_CK(launch_dslash_dd(op->call(mid, wout, true, true), op->gauge_dd.p, mid.v.data, wout.v.data, s));
-            CUDA_CK(launch_dd_to_cols32(wout.v.data, op->V, n, (char *)B->W.p + (size_t)c0 * op->wfield_bytes(),
+            CUDA_CK(launch_dd_to_cols32(wout.v.data, op->Vf, n, (char *)B->W.p + (size_t)c0 * op->wfield_bytes(),
                                         cstride, s));
         }
     } else {
         // W = A V-bar with the FP64 operator
         Field x64 = op->x64.view(1), r64f = op->b64.view(1);
         for (int c = 0; c < r; c++) {
-            Field uc = field_at(op->wprec, (char *)B->U.p + (size_t)(l + c) * op->wfield_bytes(), op->V, 1);
-            Field wc = field_at(op->wprec, (char *)B->W.p + (size_t)c * op->wfield_bytes(), op->V, 1);
+            Field uc = field_at(op->wprec, (char *)B->U.p + (size_t)(l + c) * op->wfield_bytes(), op->Vf, 1);
+            Field wc = field_at(op->wprec, (char *)B->W.p + (size_t)c * op->wfield_bytes(), op->Vf, 1);
             CUDA_CK(launch_combine(x64, 1.0, uc, 0.0, null_field(), s));
             apply_A64(op, x64, r64f, s);
             CUDA_CK(launch_combine(wc, 1.0, r64f, 0.0, null_field(), s));
@@ -1384,12 +1662,10 @@ eig_status eig_initcg_solve(eig_op op, eig_basis basis, const double *b, double 
     auto t0 = std::chrono::steady_clock::now();
     cudaStream_t s = (cudaStream_t)stream;
     Solve sv = make_solve(op, k, s, max_iter);
-    load_natural(op, b, sv.b64, s);
-    load_natural(op, x, sv.x64, s);
+    load_solve(op, b, x, sv.b64, sv.x64, s);
     const bool defl = basis && basis->l > 0;
     if (defl) {
-        apply_A64(op, sv.x64, sv.r64, s);
-        CUDA_CK(launch_combine(sv.r64, 1.0, sv.b64, -1.0, sv.r64, s));
+        sv.initial_residual();
         deflate_into(basis, sv.r64, sv.x64, s);
     }
     int restarts = 0;
@@ -1421,7 +1697,7 @@ eig_status eig_initcg_solve(eig_op op, eig_basis basis, const double *b, double 
         if (!cg_finish(sv, max_iter, nullptr, op, rounds)) break;
     }
     if (!ok) sv.true_residual(false), sv.read_scalars();
-    store_natural(op, sv.x64, x, s);
+    store_solve(op, sv.x64, x, s);
     sync(s);
     const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (stats) {
@@ -1475,7 +1751,7 @@ eig_status eig_basis_ritz(eig_basis B, double *evals, double *resnorms, int *n, 
         ColSet Wc = field_cols(B->W.p, f64, 1, B->fsize(), nc, false);
         ay_run(B, basis_cols(B, 0, l), B->Y.as<double>(), Wc, 0.0, op->ncomplex(), s);
         for (int c = 0; c < nc; c++) {
-            Field wc = field_at(op->wprec, (char *)B->W.p + (size_t)c * op->wfield_bytes(), op->V, 1);
+            Field wc = field_at(op->wprec, (char *)B->W.p + (size_t)c * op->wfield_bytes(), op->Vf, 1);
             CUDA_CK(launch_combine(x64, 1.0, wc, 0.0, null_field(), s));
             apply_A64(op, x64, r64f, s);
             CUDA_CK(launch_combine(w64, 1.0, r64f, -th[c0 + c], x64, s));
@@ -1496,7 +1772,7 @@ eig_status eig_basis_vector(eig_basis B, int j, double *out, void *stream) {
     std::lock_guard<std::mutex> lk(B->op->mu);
     eig_op_s *op = B->op;
     cudaStream_t s = (cudaStream_t)stream;
-    Field uc = field_at(op->wprec, (char *)B->U.p + (size_t)j * op->wfield_bytes(), op->V, 1);
+    Field uc = field_at(op->wprec, (char *)B->U.p + (size_t)j * op->wfield_bytes(), op->Vf, 1);
     Field x64 = op->x64.view(1);
     CUDA_CK(launch_combine(x64, 1.0, uc, 0.0, null_field(), s));
     store_natural(op, x64, out, s);
@@ -1504,10 +1780,117 @@ eig_status eig_basis_vector(eig_basis B, int j, double *out, void *stream) {
     API_END
 }
 
+eig_status eig_basis_pending(eig_basis B, double *evals, int *n) {
+    API_BEGIN
+    ARG_CHECK(B && n, "null argument");
+    *n = B->npend;
+    if (evals)
+        for (int a = 0; a < B->npend; a++) evals[a] = B->pend_ritz[a];
+    API_END
+}
+
 eig_status eig_basis_h(eig_basis B, double *out) {
     API_BEGIN
     ARG_CHECK(B && out, "null argument");
     memcpy(out, B->H.data(), B->H.size() * sizeof(cd));
+    API_END
+}
+
+eig_status eig_basis_save(eig_basis B, const char *path, void *stream) {
+    API_BEGIN
+    ARG_CHECK(B && path, "null argument");
+    std::lock_guard<std::mutex> lk(B->op->mu);
+    eig_op_s *op = B->op;
+    cudaStream_t s = (cudaStream_t)stream;
+    BasisFileHeader h;
+    memset(&h, 0, sizeof h);
+    memcpy(h.magic, BASIS_MAGIC, 8);
+    h.version = 1;
+    for (int i = 0; i < 4; i++) h.dims[i] = op->L[i];
+    h.even_odd = op->eo ? 1 : 0;
+    h.real_bytes = op->wprec == P64 ? 8 : 4;
+    h.l = B->l;
+    h.fsize = B->fsize();
+    h.m_q = op->m_q;
+    h.gauge_hash = op->gauge_hash;
+    File out;
+    out.f = fopen(path, "wb");
+    io_check(out.f != nullptr, std::string("cannot open ") + path + " for writing");
+    io_check(fwrite(&h, sizeof h, 1, out.f) == 1, "write failed");
+    const size_t nh = (size_t)B->l * B->l;
+    io_check(fwrite(B->H.data(), sizeof(cd), nh, out.f) == nh, "write failed");
+    const size_t n = (size_t)h.fsize * 2;
+    std::vector<double> v(n);
+    std::vector<float> v32(h.real_bytes == 4 ? n : 0);
+    Field x64 = op->x64.view(1);
+    for (int j = 0; j < B->l; j++) {
+        Field uc = field_at(op->wprec, (char *)B->U.p + (size_t)j * op->wfield_bytes(), op->Vf, 1);
+        CUDA_CK(launch_combine(x64, 1.0, uc, 0.0, null_field(), s));
+        store_natural(op, x64, v.data(), s);
+        sync(s);
+        if (h.real_bytes == 4) {
+            for (size_t i = 0; i < n; i++) v32[i] = (float)v[i];  // exact: FP32 storage
+            io_check(fwrite(v32.data(), 4, n, out.f) == n, "write failed");
+        } else {
+            io_check(fwrite(v.data(), 8, n, out.f) == n, "write failed");
+        }
+    }
+    const int rc = fclose(out.f);
+    out.f = nullptr;
+    io_check(rc == 0, "closing the basis file failed");
+    API_END
+}
+
+eig_status eig_basis_load(eig_basis B, const char *path, void *stream) {
+    API_BEGIN
+    ARG_CHECK(B && path, "null argument");
+    std::lock_guard<std::mutex> lk(B->op->mu);
+    eig_op_s *op = B->op;
+    cudaStream_t s = (cudaStream_t)stream;
+    File in;
+    in.f = fopen(path, "rb");
+    io_check(in.f != nullptr, std::string("cannot open ") + path);
+    BasisFileHeader h;
+    io_check(fread(&h, sizeof h, 1, in.f) == 1, "basis file too short");
+    io_check(memcmp(h.magic, BASIS_MAGIC, 8) == 0 && h.version == 1, "not a basis file of version 1");
+    for (int i = 0; i < 4; i++) ARG_CHECK(h.dims[i] == op->L[i], "basis file: lattice extents differ");
+    ARG_CHECK(h.even_odd == (op->eo ? 1 : 0), "basis file: odd-even form differs");
+    ARG_CHECK(h.m_q == op->m_q, "basis file: quark mass differs");
+    ARG_CHECK(h.gauge_hash == op->gauge_hash, "basis file: gauge field differs");
+    ARG_CHECK(h.fsize == B->fsize(), "basis file: vector length differs");
+    io_check(h.real_bytes == 4 || h.real_bytes == 8, "basis file: bad precision field");
+    io_check(h.l >= 0 && h.l <= 1 << 20, "basis file: bad basis size");
+    if (h.l > B->max_vecs) throw Error{EIG_ERR_BUDGET, "basis file holds more vectors than max_vecs"};
+    const size_t nh = (size_t)h.l * h.l;
+    std::vector<cd> H(nh);
+    io_check(fread(H.data(), sizeof(cd), nh, in.f) == nh, "basis file too short");
+    for (const cd &z : H) io_check(std::isfinite(z.real()) && std::isfinite(z.imag()), "basis file: H not finite");
+    const size_t n = (size_t)h.fsize * 2;
+    std::vector<double> v(n);
+    std::vector<float> v32(h.real_bytes == 4 ? n : 0);
+    Field x64 = op->x64.view(1);
+    // the old basis is gone from here on: an error below leaves it empty
+    B->l = 0;
+    B->H.clear();
+    B->npend = 0;
+    B->pend_ritz.clear();
+    refactor(B);
+    for (int j = 0; j < h.l; j++) {
+        if (h.real_bytes == 4) {
+            io_check(fread(v32.data(), 4, n, in.f) == n, "basis file too short");
+            for (size_t i = 0; i < n; i++) v[i] = v32[i];
+        } else {
+            io_check(fread(v.data(), 8, n, in.f) == n, "basis file too short");
+        }
+        load_natural(op, v.data(), x64, s);
+        Field uc = field_at(op->wprec, (char *)B->U.p + (size_t)j * op->wfield_bytes(), op->Vf, 1);
+        CUDA_CK(launch_combine(uc, 1.0, x64, 0.0, null_field(), s));
+        sync(s);  // v is reused for the next vector
+    }
+    B->l = h.l;
+    B->H = std::move(H);
+    refactor(B);
+    if (!B->chol_ok) throw Error{EIG_ERR_BREAKDOWN, "loaded H = U^H A U is not positive definite"};
     API_END
 }
 

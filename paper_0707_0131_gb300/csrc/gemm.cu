@@ -648,30 +648,97 @@ cudaError_t launch_window_restart(ColSet Vw, int m, const double *QZ, int nout, 
     return cudaGetLastError();
 }
 
-// w = t - beta t_prev (FP32 fields of one RHS; beta read from the device): the vector
-// A z_j of Fig. 1 step 11.8 whose dot products with the restarted window form the new
-// row of T.
+// wv[c] = sum over rows of conj(w) V[:, c] for c < nout, w = t - beta t_prev formed on
+// the fly (FP32 fields, V columns at `off` in complex units; beta read from the
+// device): Fig. 1 step 11.8 after a restart whose V <- V QZ ran elsewhere.  FP32
+// products per thread, FP64 block sums, the grid's sums added in a fixed order.
 namespace {
-__global__ void k_w_diff(const float4 *__restrict__ t, const float4 *__restrict__ tp, const double *beta_dev,
-                         float4 *__restrict__ w, long n4) {
-    const float b = (float)(*beta_dev);
-    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (long)gridDim.x * blockDim.x) {
-        const float4 x = t[i], y = tp[i];
-        w[i] = make_float4(x.x - b * y.x, x.y - b * y.y, x.z - b * y.z, x.w - b * y.w);
+template <int NO>
+__global__ void __launch_bounds__(WR_THREADS) k_wdot(const float2 *__restrict__ t, const float2 *__restrict__ tp,
+                                                     const double *beta_dev, const float2 *base, const long *off,
+                                                     int nout, long nrows, double *partials, unsigned *counter,
+                                                     double *wv) {
+    __shared__ double red[(WR_THREADS / 32) * 2];
+    const float beta = (float)(*beta_dev);
+    float2 ws[NO];
+#pragma unroll
+    for (int c = 0; c < NO; c++) ws[c] = make_float2(0.f, 0.f);
+    for (long row = (long)blockIdx.x * blockDim.x + threadIdx.x; row < nrows; row += (long)gridDim.x * blockDim.x) {
+        const float2 tv = t[row], pv = tp[row];
+        const float wr = tv.x - beta * pv.x, wi = tv.y - beta * pv.y;
+#pragma unroll
+        for (int c = 0; c < NO; c++)
+            if (c < nout) {
+                const float2 o = base[off[c] + row];
+                ws[c] = __ffma2_rn(make_float2(wr, wr), o, ws[c]);                      // conj(w) * o
+                ws[c] = __ffma2_rn(make_float2(wi, wi), make_float2(o.y, -o.x), ws[c]);
+            }
     }
+    double *Pp = partials + (long)blockIdx.x * nout * 2;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int c = 0; c < nout; c++) {
+        double vr = 0.0, vi = 0.0;
+#pragma unroll
+        for (int cc = 0; cc < NO; cc++)
+            if (cc == c) {
+                vr = (double)ws[cc].x;
+                vi = (double)ws[cc].y;
+            }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            vr += __shfl_xor_sync(0xffffffffu, vr, o);
+            vi += __shfl_xor_sync(0xffffffffu, vi, o);
+        }
+        if (lane == 0) {
+            red[warp * 2] = vr;
+            red[warp * 2 + 1] = vi;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double sr = 0.0, si = 0.0;
+            for (int w = 0; w < WR_THREADS / 32; w++) {
+                sr += red[w * 2];
+                si += red[w * 2 + 1];
+            }
+            Pp[c * 2] = sr;
+            Pp[c * 2 + 1] = si;
+        }
+        __syncthreads();
+    }
+    __shared__ bool am_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) am_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!am_last) return;
+    __threadfence();
+    for (int o = threadIdx.x; o < nout * 2; o += blockDim.x) {
+        double sum = 0.0;
+        for (unsigned b = 0; b < gridDim.x; b++) sum += __ldcg(partials + (long)b * nout * 2 + o);
+        wv[o] = sum;
+    }
+    if (threadIdx.x == 0) *counter = 0u;
 }
 }  // namespace
 
-cudaError_t launch_w_diff(const void *t, const void *t_prev, const double *beta_dev, void *w, long n_complex,
-                          cudaStream_t s) {
-    if (n_complex % 2) return cudaErrorInvalidValue;
-    ProfScope prof("w_diff", (double)n_complex * 24.0, s);
-    const long n4 = n_complex / 2;
-    long grid = (n4 + 255) / 256;
-    const long cap = (long)device_sm_count() * 8;
+cudaError_t launch_wdot(const void *t, const void *t_prev, const double *beta_dev, const void *base, const long *off,
+                        int nout, long nrows, double *wv, RedScratch red, cudaStream_t s) {
+    if (nout < 1 || nout > 32) return cudaErrorInvalidValue;
+    ProfScope prof("wdot", (double)nrows * (nout + 2) * 8.0, s);
+    long grid = (nrows + WR_THREADS - 1) / WR_THREADS;
+    long cap = (long)device_sm_count() * 4;
     if (grid > cap) grid = cap;
-    k_w_diff<<<(int)grid, 256, 0, s>>>(static_cast<const float4 *>(t), static_cast<const float4 *>(t_prev), beta_dev,
-                                       static_cast<float4 *>(w), n4);
+    const long pcap = (long)red.max_blocks * MAX_RHS * 64 / (nout * 2);
+    if (grid > pcap) grid = pcap;
+    auto t2 = static_cast<const float2 *>(t), p2 = static_cast<const float2 *>(t_prev);
+    auto b2 = static_cast<const float2 *>(base);
+#define EIG_WD(NO) \
+    k_wdot<NO><<<(int)grid, WR_THREADS, 0, s>>>(t2, p2, beta_dev, b2, off, nout, nrows, red.partials, red.counter, wv)
+    if (nout <= 8) EIG_WD(8);
+    else if (nout <= 16) EIG_WD(16);
+    else if (nout <= 24) EIG_WD(24);
+    else EIG_WD(32);
+#undef EIG_WD
     return cudaGetLastError();
 }
 

@@ -61,10 +61,18 @@ struct DslashCall {
     GaugeView gauge;
     int gformat;       // GaugeFormat
     int L[4];
-    long V;
+    long V;            // lattice sites (gauge planes hold V sites)
     int k;
     double diag;       // 4 + m_q
     bool dagger;
+    // Odd-even form (eo_parity 0 or 1; -1: the full lattice).  Fields are half-lattice
+    // fields of V / 2 sites (site s of one parity at s / 2, every extent even):
+    //   out_p = diag * cen_p + hcoef * sum over the 8 hops of in_(1-p),
+    // the hop sum being the bracket of the Wilson operator, so that the full operator
+    // is diag = 4 + m_q, hcoef = -1/2, cen = in.
+    int eo_parity = -1;
+    Field cen;
+    double hcoef = -0.5;
 };
 
 // ---------------------------- dslash.cu ----------------------------------------------
@@ -98,6 +106,8 @@ cudaError_t autotune_dslash32(const DslashCall &c, const void *const *gauge_alts
                               cudaStream_t s);
 // The link format the autotuner found faster for (V, k, storage), or -1 if not tuned.
 int dslash32_best_gformat(long V, int k, int prec);
+// Link format (-1 before tuning) and stencil variant (0..7) the call would launch with.
+int dslash32_choice(const DslashCall &c, int *variant);
 
 // dslash_dd.cu: double-float (FP32-pair) stencil for residual replacements.  dd fields
 // have the FP64 layout with float4 (re_hi, im_hi, re_lo, im_lo) per complex number.
@@ -123,6 +133,11 @@ cudaError_t launch_combine(Field out, double ca, Field a, double cb, Field b, cu
 // per-RHS ||f||^2 -> st[r].aux;  with as_rho: also rho = aux, rho_prev = aux, history rho[iter]
 // and target = tol2 * bnorm2[r] computed elsewhere (untouched here).
 cudaError_t launch_norm2(Field f, CGScalars *st, bool as_rho, History h, int iter, RedScratch red, cudaStream_t s);
+// Spectral preconditioner (Sec. 2) pieces: Y = G C for one RHS (G l x l complex
+// row-major, C and Y l complex), and rho = r^H z with Fig. 1's preconditioned scalar
+// updates for the active RHS (rho, h_rho[iter], and beta, h_beta[iter + 1] for iter >= 1).
+cudaError_t launch_sp_coef(const double *G, const double *C, double *Y, int l, cudaStream_t s);
+cudaError_t launch_pcg_rho(Field r, Field z, CGScalars *st, History h, int iter, RedScratch red, cudaStream_t s);
 // CG step 13 of the previous iteration (x += alpha p, if pending), step 9 (p = r + beta p;
 // first: p = r) and eigCG step 11.13 (v = r / sqrt(rho), optional)
 cudaError_t launch_pupdate(Field r, Field p, Field x, bool first, CGScalars *st, Field v_append, cudaStream_t s);
@@ -180,9 +195,14 @@ bool tc_ay_ok(const ColSet &A, const ColSet &Out);
 cudaError_t launch_tc_ay(const ColSet &A, const double *Y, const ColSet &Out, double beta, long nrows, int *err,
                          cudaStream_t s);
 
-// w = t - (*beta_dev) t_prev for FP32 fields of n_complex entries (n_complex even)
-cudaError_t launch_w_diff(const void *t, const void *t_prev, const double *beta_dev, void *w, long n_complex,
-                          cudaStream_t s);
+// Copies the sites of one parity between a full-lattice FP64 field and a half-lattice
+// FP64 field (to_half: full -> half), same k; Lx even.
+cudaError_t launch_parity_move(Field full, Field half, int parity, const int L[4], bool to_half, cudaStream_t s);
+
+// wv[c] = sum_rows conj(w) V[:, c] (c < nout <= 32), w = t - (*beta_dev) t_prev: FP32
+// fields of nrows complex entries, V columns at base + off[c] (complex units, device)
+cudaError_t launch_wdot(const void *t, const void *t_prev, const double *beta_dev, const void *base, const long *off,
+                        int nout, long nrows, double *wv, RedScratch red, cudaStream_t s);
 
 int device_sm_count();
 
