@@ -10,7 +10,8 @@ multiple right hand side linear systems ..."):
   solvers.py             CG and eigCG (Fig. 1, with an optional preconditioner P, Sec. 3),
                          full-history Lanczos (Eq. 4, Sec. 3.1), init-CG (Eq. 1) with its
                          restart (Sec. 5.3), Incremental eigCG and Rayleigh-Ritz on U
-                         (Sec. 4 box, Sec. 5.2), the spectral preconditioner from U (Sec. 2)
+                         (Sec. 4 box, Sec. 5.2), the spectral preconditioner from U (Sec. 2),
+                         BiCGSTAB on M deflated with eigenvectors of A through g5 M (Sec. 1)
 
 Only tests/, __graft_entry__.smoke() and the CPU-baseline leg of bench.py may
 import this package.  It shares no code with the CUDA library; the two meet only
@@ -21,7 +22,8 @@ waves, gamma5-Hermiticity, Hermiticity and positivity of A, gauge covariance,
 dense solves and eigensolves on 4^4, CG/eigCG bit-identity, T = V^H A V, Galerkin
 condition of Eq. 1, PCG against CG on the split system, the spectrum of the spectrally
 preconditioned operator in closed form, P-orthonormality of the preconditioned eigCG
-window, the Schur identity against the full operator and the free-field
+window, BiCGSTAB against dense solves and the Galerkin / invariant-subspace properties
+of the g5 M deflation, the Schur identity against the full operator and the free-field
 spectrum of the odd-site normal equations in closed form.  Parity of the eigen part at the paper's own scale (its
 figures, on ensembles that are not available) is unpinned.
 """
