@@ -64,6 +64,9 @@ def parse():
     ap.add_argument("--requests", type=int, default=200, help="serve mode: number of requests")
     ap.add_argument("--serve-lattices", default="8^4,16^3x32,24^3x64")
     ap.add_argument("--serve-basis", type=int, default=40)
+    ap.add_argument("--serve-policy", action="store_true",
+                    help="serve mode: end each operator's eigCG phase by the switch policy (expected requests "
+                         "= requests / operators) instead of at --serve-basis")
     ap.add_argument("--budget-gb", type=float, default=150.0)
     ap.add_argument("--prec", type=int, default=32)
     ap.add_argument("--reliable-delta", type=float, default=0.1,
@@ -232,14 +235,16 @@ def run_serve(a):
 
     torch.cuda.set_device(0)
     specs = []
-    for name in a.serve_lattices.split(","):
+    names = a.serve_lattices.split(",")
+    expected = a.requests // (3 * len(names)) if a.serve_policy else 0
+    for name in names:
         dims = fx.LATTICES[name]
         gauge = fx.make_gauge(dims, fx.GAUGE_SEEDS[name])
         for kappa in ("1e+03", "1e+04", "1e+05"):
             m_q, _ = mass_for(name, kappa)
             specs.append(serving.OpSpec(key=f"{name}/{kappa}", dims=dims, m_q=m_q, gauge=gauge, prec=32,
                                         max_rhs=a.k, nev=a.nev, m=a.m, basis_max=a.serve_basis, tol=a.tol,
-                                        restart_tol=a.restart_tol))
+                                        restart_tol=a.restart_tol, expected_requests=expected))
     by_key = {s.key: s for s in specs}
     rng = np.random.default_rng(105)
     keys = [specs[i].key for i in rng.integers(0, len(specs), size=a.requests)]
@@ -295,8 +300,10 @@ def run_serve(a):
            "max_true_rel_res": float(max(r["stats"]["true_rel_res"] for _, r in res)),
            "batched_fraction": float(np.mean([r["batch"] > 1 for _, r in res])),
            "max_hbm_used_gb": srv.max_used / 1e9, "budget_gb": a.budget_gb,
+           "eigcg_solves": int(sum(r["kind"] == "eigcg" for _, r in res)),
            "config": {"workload": f"{len(specs)} operators ({a.serve_lattices} x cond 1e3/1e4/1e5), basis "
-                                  f"{a.serve_basis}, eigCG({a.nev},{a.m}) then init-CG batches of <= {a.k}, tol {a.tol}"}}
+                                  f"<= {a.serve_basis}, eigCG({a.nev},{a.m}) then init-CG batches of <= {a.k}, tol {a.tol}",
+                      "switch": f"policy, {expected} expected requests per operator" if expected else "basis full"}}
     srv.close()
     print(json.dumps(out), flush=True)
 

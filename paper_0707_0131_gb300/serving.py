@@ -3,7 +3,9 @@
 Each operator keeps its own deflation basis resident on the device, so earlier
 requests deflate later ones (the incremental idea of Sec. 4): while the basis is
 still growing a request is solved with eigCG(nev, m) and its Ritz vectors are
-added (Sec. 4 box); once the basis is full, every request that is waiting for
+added (Sec. 4 box); once the basis is full, or the switch policy (policy.py, for
+operators with an expected request count) finds that more growth no longer pays
+for itself (Sec. 5.3), every request that is waiting for
 that operator is taken into one batched init-CG call (Eq. 1, restarted as in
 Sec. 5.3) of up to max_rhs right-hand sides.
 
@@ -28,6 +30,7 @@ import numpy as np
 
 from . import _lib
 from .api import Basis, Op
+from .policy import SwitchPolicy
 
 
 @dataclass
@@ -43,6 +46,11 @@ class OpSpec:
     basis_max: int = 240
     tol: float = 1e-8
     restart_tol: float = 1e-6
+    # expected number of requests for this operator: > 0 lets the switch policy of
+    # policy.py (Sec. 5.3) end the eigCG phase before basis_max when more growth no
+    # longer pays; 0 grows the basis to basis_max
+    expected_requests: int = 0
+    eigcg_overhead: float = 1.2
 
     def footprint(self) -> int:
         """Device bytes of an active operator: links, workspace, window, basis."""
@@ -77,6 +85,8 @@ class _Worker:
         self.active = False
         self.busy = False
         self.last_used = time.perf_counter()
+        self.policy = SwitchPolicy(spec.expected_requests, spec.eigcg_overhead) if spec.expected_requests > 0 else None
+        self.growing = True
         self.thread = threading.Thread(target=self._run, daemon=True, name=f"eig-{spec.key}")
         self.thread.start()
 
@@ -120,17 +130,26 @@ class _Worker:
                 self.last_used = time.perf_counter()
                 self.server._released()
 
+    def use_eigcg(self, basis_size: int) -> bool:
+        """Whether the next request grows the basis (eigCG) or joins an init-CG batch.
+        The eigCG phase ends for good at basis_max or when the switch policy says so."""
+        s = self.spec
+        if self.growing:
+            self.growing = basis_size + s.nev <= s.basis_max and (self.policy is None or self.policy.use_eigcg())
+        return self.growing
+
     def _serve(self, req: Request):
         import torch
 
         s = self.spec
-        growing = self.basis.size + s.nev <= s.basis_max
         with torch.cuda.stream(self.stream):
-            if growing:
+            if self.use_eigcg(self.basis.size):
                 b = torch.from_numpy(req.b).to("cuda", non_blocking=False)
                 x = torch.zeros_like(b)
                 st = self.op.eigcg_solve(b, x, s.nev, s.m, s.tol, basis=self.basis, stream=self.stream)
                 self.basis.grow(stream=self.stream)
+                if self.policy is not None:
+                    self.policy.record(st["iters"])
                 self._finish([req], x.reshape(1, -1), [st], "eigcg")
                 return
             batch = self._take(req, s.max_rhs)

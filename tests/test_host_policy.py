@@ -46,3 +46,28 @@ def test_policy_edge_cases():
         assert p.use_eigcg()
         p.record(300)
     assert not p.use_eigcg()
+
+
+def test_serving_worker_switch():
+    """The serving worker grows the basis while the policy (with an expected request count)
+    says so and never returns to eigCG; without a count it fills basis_max."""
+    from paper_0707_0131_gb300.serving import OpSpec, _Worker
+
+    f = lambda j: 60 + 800 * math.exp(-j / 3.0)  # noqa: E731
+    for expected, cap in [(24, 400), (0, 100)]:
+        spec = OpSpec(key="k", dims=(4, 4, 4, 4), m_q=0.1, gauge=None, nev=10, basis_max=cap,
+                      expected_requests=expected)
+        w = _Worker(None, spec)
+        size, solves = 0, 0
+        while w.use_eigcg(size):
+            if w.policy is not None:
+                w.policy.record(f(solves))
+            size += spec.nev
+            solves += 1
+        assert not w.use_eigcg(0)  # the eigCG phase does not come back
+        if expected:
+            costs = [total_cost(f, expected, k, 1.2, 0.0) for k in range(expected + 1)]
+            assert costs[solves] <= 1.02 * min(costs) and size < cap, (solves, size)
+        else:
+            assert size == cap
+        w.q.put(None)
