@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--mode", default="solve", choices=["solve", "dslash", "serve"],
+    ap.add_argument("--mode", default="solve", choices=["solve", "dslash", "serve", "bicgstab"],
                     help="dslash: only repeated matvecs through eig_op_apply (kernel GB/s); "
                          "serve: Poisson requests over 9 operators through the serving loop")
     ap.add_argument("--requests", type=int, default=200, help="serve mode: number of requests")
@@ -75,6 +75,7 @@ def parse():
                     help="FP32 link storage: 12 reals (third row rebuilt) or all 18")
     ap.add_argument("--which", type=int, default=2, help="dslash mode: 0 M, 1 M^H, 2 A")
     ap.add_argument("--reps", type=int, default=20)
+    ap.add_argument("--defl-vecs", type=int, default=64, help="bicgstab mode: Ritz vectors in the g5 M deflation")
     return ap.parse_args()
 
 
@@ -225,6 +226,54 @@ def run_dslash(a):
     op.close()
 
 
+def run_bicgstab(a):
+    """Deflated BiCGSTAB on M (Sec. 1) next to init-CG on A: a basis is grown by
+    Incremental eigCG as in the solve mode, then each of a.steps new right-hand sides of
+    M x = b is solved by BiCGSTAB without and with the g5 M deflation, and by init-CG on
+    A x = M^H b with the same basis (one RHS per call)."""
+    import torch
+
+    from paper_0707_0131_gb300.api import Basis, Op
+
+    torch.cuda.set_device(0)
+    dims = fx.LATTICES[a.lattice]
+    m_q, mass_src = mass_for(a.lattice, a.kappa)
+    gauge = fx.make_gauge(dims, fx.GAUGE_SEEDS[a.lattice])
+    op = Op(gauge, dims, m_q, prec=32, max_rhs=1)
+    basis = Basis(op, a.basis + a.nev)
+    r = 0
+    while basis.size + a.nev <= a.basis:
+        b = torch.from_numpy(fx.make_rhs(dims, fx.rhs_seed(a.lattice, r))[0].reshape(-1)).cuda()
+        op.eigcg_solve(b, torch.zeros_like(b), a.nev, a.m, a.tol, basis=basis)
+        basis.grow()
+        r += 1
+    rows = {"bicgstab": [], "bicgstab_deflated": [], "initcg": []}
+    nz = min(a.defl_vecs, basis.size)
+    for i in range(a.steps):
+        b = torch.from_numpy(fx.make_rhs(dims, fx.rhs_seed(a.lattice, 500 + i))[0].reshape(-1)).cuda()
+        bA = b.clone()
+        op.apply(1, b, bA)  # A x = M^H b has the same solution
+        for kind in rows:
+            x = torch.zeros_like(b)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            if kind == "initcg":
+                st = op.initcg_solve(bA, x, a.tol, a.restart_tol, basis=basis)[0]
+            else:
+                st = op.bicgstab_solve(b, x, a.tol, basis=basis if kind != "bicgstab" else None, defl_vecs=nz)
+            torch.cuda.synchronize()
+            rows[kind].append({"ms": (time.perf_counter() - t0) * 1e3, "iters": st["iters"],
+                               "true_rel_res": st["true_rel_res"]})
+    out = {"mode": "bicgstab", "lattice": a.lattice, "m_q": m_q, "basis": basis.size, "defl_vecs": nz,
+           "tol": a.tol, "note": "first BiCGSTAB with deflation includes building Z and Z^H g5 M Z"}
+    for kind, v in rows.items():
+        out[kind] = {"ms_mean": float(np.mean([e["ms"] for e in v])), "iters_mean": float(np.mean([e["iters"] for e in v])),
+                     "max_true_rel_res": float(max(e["true_rel_res"] for e in v)), "runs": v}
+    print(json.dumps(out), flush=True)
+    basis.close()
+    op.close()
+
+
 def run_serve(a):
     """Serving form: Poisson-arriving single-RHS requests over 3 lattices x 3 masses,
     continuous batching with per-operator resident bases under an HBM budget."""
@@ -318,6 +367,9 @@ def main():
         return
     if a.mode == "dslash":
         run_dslash(a)
+        return
+    if a.mode == "bicgstab":
+        run_bicgstab(a)
         return
     import torch
 
@@ -431,13 +483,13 @@ def main():
     traffic = None
     tfile = os.path.join(ROOT, "configs", "traffic.json")
     if os.path.exists(tfile):
-        tj = json.load(open(tfile)).get(kern, {})
         h = hashlib.sha1()
         for f in ("dslash32.cuh", "dslash32.cu", "dslash32d_rb1.cu", "dslash32d_rb2.cu"):
             h.update(open(os.path.join(ROOT, "paper_0707_0131_gb300", "csrc", f), "rb").read())
-        if (tj.get("stencil_sha1") == h.hexdigest() and tj.get("variant") == kvar
-                and tj.get("link_reals") == klinks):
-            traffic = tj["dram_over_algorithmic"] * kp["bytes"] / kp["launches"]
+        for tj in json.load(open(tfile)).get(kern, []):
+            if (tj.get("stencil_sha1") == h.hexdigest() and tj.get("variant") == kvar
+                    and tj.get("link_reals") == klinks):
+                traffic = tj["dram_over_algorithmic"] * kp["bytes"] / kp["launches"]
     roofline = {"bound": "hbm", "kernel": kern, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_src, "traffic": traffic,
                 "variant": kvar, "link_reals": klinks,

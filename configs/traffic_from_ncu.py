@@ -64,12 +64,14 @@ def main():
     ratio = sum(launches) / len(launches) / alg
     out_path = os.path.join(ROOT, "configs", "traffic.json")
     data = json.load(open(out_path)) if os.path.exists(out_path) else {}
-    data[a.name] = {"dram_over_algorithmic": ratio, "launches_captured": len(launches),
-                    "dram_bytes_per_launch": sum(launches) / len(launches), "algorithmic_bytes_per_launch": alg,
-                    "stencil_sha1": stencil_sha1(), "variant": a.variant, "link_reals": a.links,
-                    "capture": a.note}
+    entry = {"dram_over_algorithmic": ratio, "launches_captured": len(launches),
+             "dram_bytes_per_launch": sum(launches) / len(launches), "algorithmic_bytes_per_launch": alg,
+             "stencil_sha1": stencil_sha1(), "variant": a.variant, "link_reals": a.links, "capture": a.note}
+    # one entry per (variant, link form); a new capture replaces the old one
+    kept = [e for e in data.get(a.name, []) if (e["variant"], e["link_reals"]) != (a.variant, a.links)]
+    data[a.name] = kept + [entry]
     json.dump(data, open(out_path, "w"), indent=1)
-    print(json.dumps(data[a.name], indent=1))
+    print(json.dumps(entry, indent=1))
 
 
 if __name__ == "__main__":

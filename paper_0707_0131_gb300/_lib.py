@@ -71,6 +71,7 @@ SIGNATURES = {
     "eig_eigcg_solve_sp": [_P, _P, _P, _P, _I, _I, _D, _I, _I, _D, _P, _P],
     "eig_basis_grow": [_P, _P],
     "eig_basis_deflate": [_P, _P, _P, _P, _I, _P],
+    "eig_bicgstab_solve": [_P, _P, _P, _P, _D, _I, _I, _P, _P],
     "eig_initcg_solve": [_P, _P, _P, _P, _D, _D, _I, _I, _P, _P],
     "eig_basis_ritz": [_P, _P, _P, _P, _P],
     "eig_basis_vector": [_P, _I, _P, _P],
@@ -208,6 +209,15 @@ def eig_eigcg_solve_sp(op, basis, b, x, nev: int, m: int, tol: float, sp_vecs: i
     status = _check(load().eig_eigcg_solve_sp(op, basis, _ptr(b), _ptr(x), int(nev), int(m), float(tol),
                                               int(max_iter), int(sp_vecs), float(sp_shift), ctypes.byref(st),
                                               _stream(stream)))
+    d = st.as_dict()
+    d["status"] = status
+    return d
+
+
+def eig_bicgstab_solve(op, basis, b, x, tol: float, max_iter: int = 100000, defl_vecs: int = 0, stream=None):
+    st = Stats()
+    status = _check(load().eig_bicgstab_solve(op, basis, _ptr(b), _ptr(x), float(tol), int(max_iter),
+                                              int(defl_vecs), ctypes.byref(st), _stream(stream)))
     d = st.as_dict()
     d["status"] = status
     return d

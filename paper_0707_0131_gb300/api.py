@@ -69,6 +69,11 @@ class Op:
         """eigCG preconditioned by the spectral preconditioner of basis' first sp_vecs vectors."""
         return _lib.eig_eigcg_solve_sp(self.h, basis.h, b, x, nev, m, tol, sp_vecs, sp_shift, max_iter, stream)
 
+    def bicgstab_solve(self, b, x, tol, basis=None, defl_vecs=0, max_iter=100000, stream=None):
+        """BiCGSTAB on M x = b, deflated through g5 M with defl_vecs Ritz vectors of the basis."""
+        return _lib.eig_bicgstab_solve(self.h, basis.h if basis is not None else None, b, x, tol, max_iter,
+                                       defl_vecs, stream)
+
     def initcg_solve(self, b, x, tol, restart_tol=0.0, basis=None, k=1, max_iter=100000, stream=None):
         return _lib.eig_initcg_solve(self.h, basis.h if basis is not None else None, b, x, tol, restart_tol,
                                      max_iter, k, stream)

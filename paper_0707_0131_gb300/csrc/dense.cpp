@@ -392,5 +392,42 @@ void chol_solve(int n, const cd *L, cd *B, int nrhs) {
     }
 }
 
+// Gaussian elimination with partial pivoting (row interchanges): A (n x n row-major)
+// is overwritten by its LU factors, B (column-major n x nrhs) by the solution.
+bool lu_solve(int n, cd *A, cd *B, int nrhs) {
+    std::vector<int> piv(n);
+    for (int j = 0; j < n; j++) {
+        int pr = j;
+        double best = std::abs(A[(size_t)j * n + j]);
+        for (int i = j + 1; i < n; i++)
+            if (std::abs(A[(size_t)i * n + j]) > best) {
+                best = std::abs(A[(size_t)i * n + j]);
+                pr = i;
+            }
+        if (!(best > 0.0) || !std::isfinite(best)) return false;
+        piv[j] = pr;
+        if (pr != j)
+            for (int k = 0; k < n; k++) std::swap(A[(size_t)j * n + k], A[(size_t)pr * n + k]);
+        const cd d = A[(size_t)j * n + j];
+        for (int i = j + 1; i < n; i++) {
+            const cd f = A[(size_t)i * n + j] / d;
+            A[(size_t)i * n + j] = f;
+            for (int k = j + 1; k < n; k++) A[(size_t)i * n + k] -= f * A[(size_t)j * n + k];
+        }
+    }
+    for (int c = 0; c < nrhs; c++) {
+        cd *b = B + (size_t)c * n;
+        for (int j = 0; j < n; j++)
+            if (piv[j] != j) std::swap(b[j], b[piv[j]]);
+        for (int i = 0; i < n; i++)
+            for (int k = 0; k < i; k++) b[i] -= A[(size_t)i * n + k] * b[k];
+        for (int i = n - 1; i >= 0; i--) {
+            for (int k = i + 1; k < n; k++) b[i] -= A[(size_t)i * n + k] * b[k];
+            b[i] /= A[(size_t)i * n + i];
+        }
+    }
+    return true;
+}
+
 }  // namespace dense
 }  // namespace eig

@@ -42,6 +42,10 @@ bool cholesky(int n, cd *L);
 // Solves L L^H X = B for nrhs columns (B column-major n x nrhs, overwritten).
 void chol_solve(int n, const cd *L, cd *B, int nrhs);
 
+// Solves A X = B by Gaussian elimination with partial pivoting (A n x n row-major,
+// overwritten; B column-major n x nrhs, overwritten).  false if A is singular.
+bool lu_solve(int n, cd *A, cd *B, int nrhs);
+
 // Orthonormalises the columns of X (n x c column-major) by modified Gram-Schmidt
 // applied twice; a column whose norm after projection is below drop_tol times its
 // original norm is dropped.  Kept columns are compacted to the front; returns

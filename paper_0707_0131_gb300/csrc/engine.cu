@@ -193,6 +193,10 @@ struct eig_op_s {
     FieldBuf zsp;
     DevBuf spG, spC, spY, sptc, sperr;
     PinBuf sperrh;
+    // BiCGSTAB: r_hat, s, t (one RHS, Krylov precision) and the device scalars
+    FieldBuf bc_rh, bc_s, bc_t;
+    DevBuf bsc;
+    PinBuf bsch;
     DevBuf jbase_dev;  // iteration base the replayed kernels add to their offsets
     PinBuf jbase_h;
     cudaStream_t cap_stream = nullptr;  // private stream the graphs are captured on
@@ -270,6 +274,13 @@ struct eig_basis_s {
     DevBuf C, Y;            // device small matrices
     DevBuf tcpart, tcerr;   // partial sums and error flag of the tensor-core U^H R
     PinBuf Ch, errh;
+    long gen = 0;           // bumped whenever U changes
+    // BiCGSTAB deflation through g5 M: Z = lowest Ritz vectors of A in span(U) and
+    // H5 = Z^H g5 M Z, valid for generation z_gen and z_n vectors
+    DevBuf Z;
+    std::vector<cd> H5;
+    int z_n = 0;
+    long z_gen = -1;
     std::mutex mu;
     long fsize() const { return op->Vf * 12; }  // complex entries per field
 };
@@ -656,6 +667,7 @@ static cudaGraphExec_t cg_graph(Solve &sv, eig_op_s *op) {
 
 static ColSet basis_cols(eig_basis_s *B, int first, int n);
 
+
 // z = P^{-1} r = r + U_p (G (U_p^H r)) with the spectral preconditioner of the first spl
 // basis vectors, then rho = r^H z and beta_j (Fig. 1 steps 3-4 and 8 in preconditioned
 // form; iter = the last finished iteration).  No host synchronisation: the contractions'
@@ -1041,6 +1053,73 @@ static void deflate_into(eig_basis_s *B, Field r64, Field x64, cudaStream_t s) {
     sync(s);  // Yr must outlive the async copy
 }
 
+// ------------------------------------------------------------------------------------
+// BiCGSTAB on M deflated through g5 M (Sec. 1: A = M^H M = (g5 M)^2, so eigenvectors of
+// A are eigenvectors of the Hermitian g5 M)
+// ------------------------------------------------------------------------------------
+// Z = the nz lowest Ritz vectors of A in span(U) (U S, H S = S Theta) and
+// H5 = Z^H g5 M Z, kept until U changes.
+static void g5_setup(eig_basis_s *B, int nz, cudaStream_t s) {
+    if (B->z_gen == B->gen && B->z_n == nz) return;
+    eig_op_s *op = B->op;
+    const int l = B->l;
+    const bool f64 = op->wprec == P64;
+    const long nrow = op->ncomplex();
+    const size_t wfb = op->wfield_bytes();
+    std::vector<double> th(nz);
+    std::vector<cd> S((size_t)l * nz);
+    dense::herm_eig_lowest(l, B->H.data(), nz, th.data(), S.data());
+    std::vector<double> yr((size_t)l * nz * 2);
+    for (int a = 0; a < l; a++)
+        for (int c = 0; c < nz; c++) {
+            yr[((size_t)a * nz + c) * 2] = S[(size_t)c * l + a].real();
+            yr[((size_t)a * nz + c) * 2 + 1] = S[(size_t)c * l + a].imag();
+        }
+    B->Y.ensure(yr.size() * sizeof(double));
+    CUDA_CK(cudaMemcpyAsync(B->Y.p, yr.data(), yr.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    B->Z.ensure((size_t)nz * wfb);
+    const ColSet Zc = field_cols(B->Z.p, f64, 1, B->fsize(), nz, false);
+    ay_run(B, basis_cols(B, 0, l), B->Y.as<double>(), Zc, 0.0, nrow, s);
+    sync(s);  // yr must outlive the async copy
+    std::vector<cd> H5((size_t)nz * nz);
+    for (int c0 = 0; c0 < nz; c0 += MAX_NEV) {
+        const int nc = std::min(MAX_NEV, nz - c0);
+        for (int j = 0; j < nc; j++) {  // W_j = g5 M z_(c0 + j)
+            Field zj = field_at(op->wprec, (char *)B->Z.p + (size_t)(c0 + j) * wfb, op->Vf, 1);
+            Field wj = field_at(op->wprec, (char *)B->W.p + (size_t)j * wfb, op->Vf, 1);
+            apply_M(op, zj, wj, false, f64, s);
+            CUDA_CK(launch_gamma5(wj, wj, s));
+        }
+        const cd *C = ahb_to_host(B, Zc, field_cols(B->W.p, f64, 1, B->fsize(), nc, false), nrow, s);
+        for (int a = 0; a < nz; a++)
+            for (int c = 0; c < nc; c++) H5[(size_t)a * nz + c0 + c] = C[(size_t)a * nc + c];
+    }
+    B->H5 = std::move(H5);
+    B->z_n = nz;
+    B->z_gen = B->gen;
+}
+
+// x64 += Z H5^{-1} Z^H g5 r64: the Galerkin condition of Eq. 1 for g5 M x = g5 b on span(Z)
+static void g5_deflate(eig_basis_s *B, Field r64, Field x64, cudaStream_t s) {
+    eig_op_s *op = B->op;
+    const int nz = B->z_n;
+    const bool f64 = op->wprec == P64;
+    const long nrow = op->ncomplex();
+    Field rsv = op->rsv.view(1);
+    CUDA_CK(launch_combine(rsv, 1.0, r64, 0.0, null_field(), s));
+    CUDA_CK(launch_gamma5(rsv, rsv, s));
+    const ColSet Zc = field_cols(B->Z.p, f64, 1, B->fsize(), nz, false);
+    const cd *C = ahb_to_host(B, Zc, field_cols(rsv.v.data, f64, 1, B->fsize(), 1, true), nrow, s);
+    std::vector<cd> A5 = B->H5, y(C, C + nz);
+    if (!dense::lu_solve(nz, A5.data(), y.data(), 1)) throw Error{EIG_ERR_BREAKDOWN, "Z^H g5 M Z is singular"};
+    B->Y.ensure((size_t)nz * 16);
+    CUDA_CK(cudaMemcpyAsync(B->Y.p, y.data(), (size_t)nz * 16, cudaMemcpyHostToDevice, s));
+    Field xsv = op->xsv.view(1);
+    ay_run(B, Zc, B->Y.as<double>(), field_cols(xsv.v.data, f64, 1, B->fsize(), 1, true), 0.0, nrow, s);
+    CUDA_CK(launch_combine(x64, 1.0, x64, 1.0, xsv, s));
+    sync(s);  // y must outlive the async copy
+}
+
 }  // namespace eig
 
 // ------------------------------------------------------------------------------------
@@ -1338,6 +1417,7 @@ eig_status eig_basis_truncate(eig_basis basis, int l) {
         for (int b = 0; b < l; b++) H[(size_t)a * l + b] = basis->H[(size_t)a * old + b];
     basis->H = H;
     basis->l = l;
+    basis->gen++;
     basis->npend = 0;
     refactor(basis);
     API_END
@@ -1620,6 +1700,7 @@ eig_status eig_basis_grow(eig_basis B, void *stream) {
         }
     B->H = Hn;
     B->l = ln;
+    B->gen++;
     B->npend = 0;
     refactor(B);
     if (!B->chol_ok) throw Error{EIG_ERR_BREAKDOWN, "H = U^H A U lost positive definiteness"};
@@ -1715,6 +1796,114 @@ eig_status eig_initcg_solve(eig_op op, eig_basis basis, const double *b, double 
     }
     if (!ok) {
         eig::g_last_error = "max_iter reached";
+        return EIG_NOT_CONVERGED;
+    }
+    API_END
+}
+
+eig_status eig_bicgstab_solve(eig_op op, eig_basis basis, const double *b, double *x, double tol, int max_iter,
+                              int defl_vecs, eig_stats *stats, void *stream) {
+    API_BEGIN
+    ARG_CHECK(op && b && x, "null argument");
+    ARG_CHECK(!op->eo, "BiCGSTAB runs on the full-lattice M (even_odd = 0)");
+    ARG_CHECK(op->prec != P16, "BiCGSTAB needs an FP64 or FP32 op");
+    ARG_CHECK(tol > 0.0 && tol < 1.0, "tol must be in (0, 1)");
+    ARG_CHECK(max_iter >= 1 && max_iter <= 10000000, "max_iter out of range");
+    ARG_CHECK(defl_vecs >= 0, "defl_vecs must be >= 0");
+    ARG_CHECK(!basis || basis->op == op, "basis belongs to another op");
+    std::lock_guard<std::mutex> lk(op->mu);
+    auto t0 = std::chrono::steady_clock::now();
+    cudaStream_t s = (cudaStream_t)stream;
+    if (op->prec != P64) tune_for(op, 1, s);
+    const bool f64 = op->prec == P64;
+    Field b64 = op->b64.view(1), x64 = op->x64.view(1), rt = op->u64.view(1);
+    Field r = op->r.view(1), p = op->p.view(1), v = op->u.view(1);
+    if (op->bc_rh.kcap < 1) {
+        op->bc_rh.alloc(op->prec, op->Vf, 1);
+        op->bc_s.alloc(op->prec, op->Vf, 1);
+        op->bc_t.alloc(op->prec, op->Vf, 1);
+    }
+    Field rh = op->bc_rh.view(1), sf = op->bc_s.view(1), tf = op->bc_t.view(1);
+    op->bsc.ensure(sizeof(BicgScalars));
+    op->bsch.ensure(sizeof(BicgScalars));
+    BicgScalars *sc = op->bsc.as<BicgScalars>(), *sch = op->bsch.as<BicgScalars>();
+    CGScalars *cst = op->st.as<CGScalars>(), *csth = op->st_h.as<CGScalars>();
+    const RedScratch red = op->red();
+    load_natural(op, b, b64, s);
+    load_natural(op, x, x64, s);
+    // ||r||^2 of a FP64 field through the CG scalars' aux slot
+    auto norm2_64 = [&](Field f) {
+        CUDA_CK(launch_norm2(f, cst, false, History(), 0, red, s));
+        CUDA_CK(cudaMemcpyAsync(csth, cst, sizeof(CGScalars), cudaMemcpyDeviceToHost, s));
+        sync(s);
+        return csth->aux;
+    };
+    auto true_residual = [&]() {  // rt = b - M x in FP64
+        apply_M(op, x64, rt, false, true, s);
+        CUDA_CK(launch_combine(rt, 1.0, b64, -1.0, rt, s));
+        return norm2_64(rt);
+    };
+    const double bn2 = norm2_64(b64);
+    if (basis && basis->l > 0 && defl_vecs > 0) {
+        g5_setup(basis, std::min(defl_vecs, basis->l), s);
+        true_residual();
+        g5_deflate(basis, rt, x64, s);
+    }
+    // FP32 Krylov vectors track the true residual to a few decades: restart from the
+    // FP64 residual when the recursive one has fallen by 1e5
+    const double rel_inner = f64 ? 0.0 : 1e-5;
+    int total = 0, restarts = 0;
+    double rr_true = 0.0;
+    bool ok = false;
+    while (true) {
+        rr_true = true_residual();
+        if (rr_true <= tol * tol * bn2 || bn2 == 0.0) {
+            ok = true;
+            break;
+        }
+        if (total >= max_iter || restarts > 30) break;
+        CUDA_CK(launch_combine(r, 1.0, rt, 0.0, null_field(), s));
+        CUDA_CK(launch_combine(rh, 1.0, r, 0.0, null_field(), s));
+        zero_field(p, s);
+        zero_field(v, s);
+        memset(sch, 0, sizeof(BicgScalars));
+        sch->rho[0] = rr_true;
+        sch->alpha[0] = 1.0;
+        sch->omega[0] = 1.0;
+        sch->rr = rr_true;
+        sch->target = std::max(tol * tol * bn2, rel_inner * rel_inner * rr_true);
+        sch->active = 1;
+        CUDA_CK(cudaMemcpyAsync(sc, sch, sizeof(BicgScalars), cudaMemcpyHostToDevice, s));
+        while (true) {
+            for (int c = 0; c < CHECK; c++) {
+                CUDA_CK(launch_bicg_p(r, p, v, sc, s));
+                apply_M(op, p, v, false, f64, s);
+                CUDA_CK(launch_bicg_alpha(rh, v, sc, red, s));
+                CUDA_CK(launch_bicg_s(r, v, sf, sc, s));
+                apply_M(op, sf, tf, false, f64, s);
+                CUDA_CK(launch_bicg_omega(tf, sf, sc, red, s));
+                CUDA_CK(launch_bicg_update(x64, p, sf, tf, r, rh, sc, red, s));
+            }
+            CUDA_CK(cudaMemcpyAsync(sch, sc, sizeof(BicgScalars), cudaMemcpyDeviceToHost, s));
+            sync(s);
+            if (!sch->active || total + sch->iters >= max_iter) break;
+        }
+        total += sch->iters;
+        restarts++;
+    }
+    store_natural(op, x64, x, s);
+    sync(s);
+    if (stats) {
+        stats->iters = total;
+        stats->restarts = std::max(0, restarts - 1);
+        stats->reliable_updates = restarts;
+        stats->true_rel_res = bn2 > 0 ? std::sqrt(rr_true / bn2) : 0.0;
+        stats->converged = ok ? 1 : 0;
+        stats->n_ritz = 0;
+        stats->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
+    if (!ok) {
+        eig::g_last_error = "BiCGSTAB did not reach tol within max_iter";
         return EIG_NOT_CONVERGED;
     }
     API_END
@@ -1871,6 +2060,7 @@ eig_status eig_basis_load(eig_basis B, const char *path, void *stream) {
     Field x64 = op->x64.view(1);
     // the old basis is gone from here on: an error below leaves it empty
     B->l = 0;
+    B->gen++;
     B->H.clear();
     B->npend = 0;
     B->pend_ritz.clear();

@@ -33,6 +33,20 @@ struct CGScalars {
     int breakdown;    // 1 if pAp <= 0, NaN or Inf was met
 };
 
+// Device scalars of one BiCGSTAB solve (complex values as re, im).
+struct BicgScalars {
+    double rho[2];    // r_hat^H r
+    double alpha[2];  // rho / (r_hat^H v)
+    double omega[2];  // (t^H s) / (t^H t)
+    double beta[2];   // (rho' / rho) (alpha / omega)
+    double rr;        // ||r||^2 of the recursive residual
+    double target;    // stop when rr <= target
+    int active;       // 1 while iterating
+    int breakdown;    // 1 if a denominator vanished or a NaN/Inf appeared
+    int iters;        // iterations completed
+    int pad;
+};
+
 // Reduction scratch shared by the kernels of one solver stream.
 struct RedScratch {
     double *partials;   // [max_blocks * MAX_RHS * 64] doubles
@@ -133,6 +147,17 @@ cudaError_t launch_combine(Field out, double ca, Field a, double cb, Field b, cu
 // per-RHS ||f||^2 -> st[r].aux;  with as_rho: also rho = aux, rho_prev = aux, history rho[iter]
 // and target = tol2 * bnorm2[r] computed elsewhere (untouched here).
 cudaError_t launch_norm2(Field f, CGScalars *st, bool as_rho, History h, int iter, RedScratch red, cudaStream_t s);
+// bicgstab.cu: the BiCGSTAB steps on one RHS (see there); x64 FP64, the other fields
+// in one storage precision (FP64 or FP32)
+cudaError_t launch_bicg_p(Field r, Field p, Field v, const BicgScalars *sc, cudaStream_t s);
+cudaError_t launch_bicg_alpha(Field rh, Field v, BicgScalars *sc, RedScratch red, cudaStream_t s);
+cudaError_t launch_bicg_s(Field r, Field v, Field sv, const BicgScalars *sc, cudaStream_t s);
+cudaError_t launch_bicg_omega(Field t, Field sv, BicgScalars *sc, RedScratch red, cudaStream_t s);
+cudaError_t launch_bicg_update(Field x64, Field p, Field sv, Field t, Field r, Field rh, BicgScalars *sc,
+                               RedScratch red, cudaStream_t s);
+// out = g5 in (chiral basis, g5 = diag(1, 1, -1, -1) in spin); FP64 or FP32 fields
+cudaError_t launch_gamma5(Field in, Field out, cudaStream_t s);
+
 // Spectral preconditioner (Sec. 2) pieces: Y = G C for one RHS (G l x l complex
 // row-major, C and Y l complex), and rho = r^H z with Fig. 1's preconditioned scalar
 // updates for the active RHS (rho, h_rho[iter], and beta, h_beta[iter + 1] for iter >= 1).

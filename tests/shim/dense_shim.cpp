@@ -19,6 +19,7 @@ int shim_cholesky_solve(int n, cd *H, cd *B, int nrhs) {
     eig::dense::chol_solve(n, H, B, nrhs);
     return 1;
 }
+int shim_lu_solve(int n, cd *A, cd *B, int nrhs) { return eig::dense::lu_solve(n, A, B, nrhs) ? 1 : 0; }
 int shim_orth_columns(int n, int c, cd *X, double drop, int *keep) { return eig::dense::orth_columns(n, c, X, drop, keep); }
 void shim_tridiag_eig(int n, const double *d, const double *e, int lo, int hi, double *w, double *Z) {
     eig::dense::tridiag_eig(n, d, e, lo, hi, w, Z);

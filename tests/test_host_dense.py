@@ -32,6 +32,8 @@ def lib():
     L.shim_restart_coefficients.argtypes = [I, V, I, I, D, V, V]
     L.shim_cholesky_solve.argtypes = [I, V, V, I]
     L.shim_orth_columns.argtypes = [I, I, V, D, V]
+    L.shim_lu_solve.argtypes = [I, V, V, I]
+    L.shim_lu_solve.restype = ctypes.c_int
     L.shim_tridiag_eig.argtypes = [I, V, V, I, I, V, V]
     L.shim_restart_coefficients.restype = ctypes.c_int
     L.shim_cholesky_solve.restype = ctypes.c_int
@@ -174,3 +176,25 @@ def test_cholesky_solve_and_orth(lib):
     assert r == 2 and list(keep[:2]) == [0, 1]
     Q = Xc[:2].T
     assert np.max(np.abs(Q.conj().T @ Q - np.eye(2))) < 1e-13
+
+
+@pytest.mark.parametrize("n", [1, 7, 64, 200])
+def test_lu_solve_indefinite(lib, n):
+    """Hermitian indefinite systems (the g5-M Galerkin matrix of the BiCGSTAB deflation)
+    and a singular one."""
+    rng = np.random.default_rng(n)
+    A = rand_herm(rng, n)
+    B = rng.standard_normal((n, 3)) + 1j * rng.standard_normal((n, 3))
+    Af = np.ascontiguousarray(A.copy())
+    Bc = np.ascontiguousarray(B.T.copy())  # column-major n x 3
+    assert lib.shim_lu_solve(n, P(Af), P(Bc), 3) == 1
+    X = np.linalg.solve(A, B)
+    assert np.linalg.norm(Bc.T - X) <= 1e-10 * np.linalg.cond(A) * np.linalg.norm(X)
+    S = np.zeros((n, n), dtype=np.complex128)  # exactly singular: refused
+    S[:, 1:] = A[:, 1:]
+    S[0, 0] = 0.0
+    S[1:, 0] = 0.0
+    if n > 1:
+        S[:, 0] = 0.0
+    Bs = np.ascontiguousarray(B[:, :1].T.copy())
+    assert lib.shim_lu_solve(n, P(np.ascontiguousarray(S)), P(Bs), 1) == 0
