@@ -69,7 +69,7 @@ def parse():
                          "= requests / operators) instead of at --serve-basis")
     ap.add_argument("--budget-gb", type=float, default=150.0)
     ap.add_argument("--prec", type=int, default=32)
-    ap.add_argument("--reliable-delta", type=float, default=0.1,
+    ap.add_argument("--reliable-delta", type=float, default=0.01,
                     help="residual replacement when ||r|| fell by this factor since the last one")
     ap.add_argument("--links", type=int, default=12, choices=[12, 18],
                     help="FP32 link storage: 12 reals (third row rebuilt) or all 18")

@@ -67,8 +67,9 @@ def main():
     entry = {"dram_over_algorithmic": ratio, "launches_captured": len(launches),
              "dram_bytes_per_launch": sum(launches) / len(launches), "algorithmic_bytes_per_launch": alg,
              "stencil_sha1": stencil_sha1(), "variant": a.variant, "link_reals": a.links, "capture": a.note}
-    # one entry per (variant, link form); a new capture replaces the old one
-    kept = [e for e in data.get(a.name, []) if (e["variant"], e["link_reals"]) != (a.variant, a.links)]
+    # one entry per (stencil sources, variant, link form); a new capture replaces the old one
+    key = (entry["stencil_sha1"], a.variant, a.links)
+    kept = [e for e in data.get(a.name, []) if (e["stencil_sha1"], e["variant"], e["link_reals"]) != key]
     data[a.name] = kept + [entry]
     json.dump(data, open(out_path, "w"), indent=1)
     print(json.dumps(entry, indent=1))

@@ -174,6 +174,20 @@ eig_status eig_basis_deflate(eig_basis basis, const double *b, const double *x_i
 eig_status eig_initcg_solve(eig_op op, eig_basis basis, const double *b, double *x, double tol, double restart_tol,
                             int max_iter, int k, eig_stats *stats, void *stream);
 
+/* BiCGSTAB (van der Vorst 1992) on M x = b for one RHS, deflated with the basis as Sec. 1
+ * proposes: A = M^H M = (g5 M)^2, so the eigenvectors eigCG computes for A are
+ * eigenvectors of the Hermitian g5 M.  With defl_vecs > 0 and a non-empty basis, the
+ * initial guess x~0 (in x) becomes x0 = x~0 + Z (Z^H g5 M Z)^{-1} Z^H g5 (b - M x~0),
+ * Z = the min(defl_vecs, l) lowest Ritz vectors of A in span(U) (cached with
+ * Z^H g5 M Z until the basis changes).  b, x: natural layout, full lattice.  Vectors in
+ * the op's storage precision (FP64 or FP32), x in FP64; FP32 runs restart from the FP64
+ * residual b - M x whenever the recursive residual has fallen by 1e5, and every solve
+ * ends with the FP64 residual ||b - M x|| <= tol ||b|| (true_rel_res refers to M).
+ * stats->restarts counts those restarts and breakdown restarts.  Odd-even and FP16 ops
+ * are refused (EIG_ERR_ARG).  EIG_NOT_CONVERGED after max_iter iterations. */
+eig_status eig_bicgstab_solve(eig_op op, eig_basis basis, const double *b, double *x, double tol, int max_iter,
+                              int defl_vecs, eig_stats *stats, void *stream);
+
 /* Rayleigh-Ritz on U (Sec. 5.2): Ritz values (eigenvalues of H, ascending) and
  * residual norms ||A u - theta u|| (FP64 operator).  evals/resnorms: host arrays of
  * at least l entries (resnorms may be NULL to skip the residuals); *n = l. */

@@ -1069,18 +1069,22 @@ static void g5_setup(eig_basis_s *B, int nz, cudaStream_t s) {
     std::vector<double> th(nz);
     std::vector<cd> S((size_t)l * nz);
     dense::herm_eig_lowest(l, B->H.data(), nz, th.data(), S.data());
-    std::vector<double> yr((size_t)l * nz * 2);
-    for (int a = 0; a < l; a++)
-        for (int c = 0; c < nz; c++) {
-            yr[((size_t)a * nz + c) * 2] = S[(size_t)c * l + a].real();
-            yr[((size_t)a * nz + c) * 2 + 1] = S[(size_t)c * l + a].imag();
-        }
-    B->Y.ensure(yr.size() * sizeof(double));
-    CUDA_CK(cudaMemcpyAsync(B->Y.p, yr.data(), yr.size() * sizeof(double), cudaMemcpyHostToDevice, s));
     B->Z.ensure((size_t)nz * wfb);
     const ColSet Zc = field_cols(B->Z.p, f64, 1, B->fsize(), nz, false);
-    ay_run(B, basis_cols(B, 0, l), B->Y.as<double>(), Zc, 0.0, nrow, s);
-    sync(s);  // yr must outlive the async copy
+    for (int c0 = 0; c0 < nz; c0 += MAX_NEV) {  // Z = U S, MAX_NEV columns per pass over U
+        const int nc = std::min(MAX_NEV, nz - c0);
+        std::vector<double> yr((size_t)l * nc * 2);
+        for (int a = 0; a < l; a++)
+            for (int c = 0; c < nc; c++) {
+                yr[((size_t)a * nc + c) * 2] = S[(size_t)(c0 + c) * l + a].real();
+                yr[((size_t)a * nc + c) * 2 + 1] = S[(size_t)(c0 + c) * l + a].imag();
+            }
+        B->Y.ensure(yr.size() * sizeof(double));
+        CUDA_CK(cudaMemcpyAsync(B->Y.p, yr.data(), yr.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+        const ColSet Zpart = field_cols((char *)B->Z.p + (size_t)c0 * wfb, f64, 1, B->fsize(), nc, false);
+        ay_run(B, basis_cols(B, 0, l), B->Y.as<double>(), Zpart, 0.0, nrow, s);
+        sync(s);  // yr must outlive the async copy
+    }
     std::vector<cd> H5((size_t)nz * nz);
     for (int c0 = 0; c0 < nz; c0 += MAX_NEV) {
         const int nc = std::min(MAX_NEV, nz - c0);
