@@ -95,6 +95,23 @@ def rank_info():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def max_over_ranks(ms, world, device):
+    """The slowest rank's time (every rank gets it): replicas finish when the last one does."""
+    if world == 1:
+        return float(ms)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(ms)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, steps, rhs_per_step, ms):
+    """Whole-job RHS/s: every replica solves steps * rhs_per_step RHS in the slowest time."""
+    return world * steps * rhs_per_step / (ms / 1e3)
+
+
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
 
@@ -396,7 +413,9 @@ def main():
     m_q, mass_src = mass_for(a.lattice, a.kappa)
     gauge = fx.make_gauge(dims, fx.GAUGE_SEEDS[a.lattice])
     k = a.k
-    op = Op(gauge, dims, m_q, prec=32, max_rhs=k, compress12=a.links == 12, reliable_delta=a.reliable_delta)
+    if a.prec not in (32, 16):
+        raise SystemExit("the solve benchmark stores spinors in FP32 or FP16 (--prec 32|16)")
+    op = Op(gauge, dims, m_q, prec=a.prec, max_rhs=k, compress12=a.links == 12, reliable_delta=a.reliable_delta)
     basis = Basis(op, a.basis + a.nev)
     nrhs_id = [0]
 
@@ -454,15 +473,9 @@ def main():
     clk = clocks.stop()
     _lib.eig_profile_enable(False)
     prof = _lib.eig_profile_read()
-    ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1), world, dev)
     rhs_per_step = 1 + k
-    value = world * a.steps * rhs_per_step / (ms / 1e3)
+    value = job_rate(world, a.steps, rhs_per_step, ms)
     launches = int(sum(v["launches"] for v in prof.values()))
     # dominant kernel roofline (HBM-bound stencil)
     kern = max((n for n in prof if n.startswith("dslash")), key=lambda n: prof[n]["ms"])
@@ -548,7 +561,8 @@ def main():
                "config": {"workload": f"{a.lattice} Wilson, m_q={m_q} ({mass_src}, cond(A)~{a.kappa}), "
                                       f"per step 1 eigCG({a.nev},{a.m}) + grow + k={k} batched init-CG, "
                                       f"basis {l0} FP32 vectors, tol {a.tol}, restart {a.restart_tol}",
-                          "lattice": a.lattice, "k": k, "basis": l0, "storage": "fp32 spinors, fp32 links (12- and 18-real resident, chosen per k by the autotuner), "
+                          "lattice": a.lattice, "k": k, "basis": l0, "storage": ("fp32 spinors, fp32 links (12- and 18-real resident, chosen per k by the autotuner), " if a.prec == 32 else
+                                     "fp16 spinors with one fp32 scale per site, fp16 12-real links, fp32 eigCG window and basis, ") +
                           f"double-float residual replacements (delta {a.reliable_delta}), fp64 final residual", "l2": "inputs larger than L2 (each field >= 85 MB)",
                           "parallelism": f"replicas{world}"},
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,

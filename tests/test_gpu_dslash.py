@@ -4,7 +4,8 @@ Relative error ||y_gpu - y_oracle|| / ||y_oracle|| per RHS: FP64 <= 1e-12, FP32
 <= 1e-6, FP16 storage <= 5e-3, for M, M^H and A = M^H M, single and multi-RHS.
 Lattices: 4^4, an anisotropic 6x4x2x10 (extents 2 and a site count that is not a
 multiple of the block size), 8^4, and the 24^3x64 workload of the benchmark at
-k = 16 in FP32 with 12-real links.
+k = 16 in FP32, before and after the autotuner has picked the benchmark's variant and
+link form, with a 16-RHS solve to 1e-8 checked against the oracle's FP64 residual.
 """
 import json
 import os
@@ -93,6 +94,20 @@ def test_matvec_bench_workload_fp32_k16(api):
     out = d_out.cpu().numpy()
     for r in (0, 7, 15):
         assert _relerr(out[r].reshape(-1), W.A(psi[r])) < 1e-6
+    # a batched solve tunes the stencil as the benchmark does; the tuned variant and
+    # link form must give the same products, and the solve itself (CG epilogues in
+    # that launch configuration) must meet 1e-8 in the oracle's FP64 residual
+    X = torch.zeros_like(d_in)
+    sts = op.initcg_solve(d_in, X, 1e-8, k=16)
+    v, links = op.stencil_choice(16)
+    assert v >= 0 and links in (12, 18)
+    op.apply(2, d_in, d_out, 16)
+    out = d_out.cpu().numpy()
+    x = X.cpu().numpy()
+    for r in (0, 7, 15):
+        assert _relerr(out[r].reshape(-1), W.A(psi[r])) < 1e-6, (r, v, links)
+        b = psi[r].reshape(-1)
+        assert np.linalg.norm(b - W.A(x[r].reshape(-1))) / np.linalg.norm(b) <= 1e-8 * (1 + 1e-6), (r, sts[r])
     op.close()
 
 
