@@ -61,3 +61,16 @@ def test_oracle_and_cuda_path_share_no_code():
             txt = open(os.path.join(ROOT, "oracle", f)).read()
             assert "paper_0707_0131_gb300" not in txt, f
             assert "csrc" not in txt, f
+
+
+def test_header_is_plain_c(tmp_path):
+    """include/eigcg.h compiles as C99 and as C++ (no CUDA or torch types in the boundary)."""
+    import subprocess
+
+    src = tmp_path / "use.c"
+    src.write_text('#include "eigcg.h"\nint main(void) { eig_op op = 0; (void)op; return EIG_OK; }\n')
+    inc = os.path.join(ROOT, "include")
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-fsyntax-only", "-I", inc, str(src)], check=True)
+    cpp = tmp_path / "use.cpp"
+    cpp.write_text(src.read_text())
+    subprocess.run(["g++", "-std=c++17", "-Wall", "-Werror", "-fsyntax-only", "-I", inc, str(cpp)], check=True)
