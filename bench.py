@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-serve", action="store_true", help="skip the short serving phase of the solve benchmark")
+    ap.add_argument("--serve-requests", type=int, default=48, help="solve mode: requests of the serving phase")
     ap.add_argument("--mode", default="solve", choices=["solve", "dslash", "serve", "bicgstab"],
                     help="dslash: only repeated matvecs through eig_op_apply (kernel GB/s); "
                          "serve: Poisson requests over 9 operators through the serving loop")
@@ -365,6 +367,7 @@ def run_serve(a):
            "plain_fp64_eigcg_ms_per_request_mean": plain_mean,
            "max_true_rel_res": float(max(r["stats"]["true_rel_res"] for _, r in res)),
            "batched_fraction": float(np.mean([r["batch"] > 1 for _, r in res])),
+           "batch_histogram": srv.batch_histogram(),
            "max_hbm_used_gb": srv.max_used / 1e9, "budget_gb": a.budget_gb,
            "eigcg_solves": int(sum(r["kind"] == "eigcg" for _, r in res)),
            "config": {"workload": f"{len(specs)} operators ({a.serve_lattices} x cond 1e3/1e4/1e5), basis "
@@ -438,6 +441,14 @@ def main():
     setup_s = time.perf_counter() - t0
     l0 = basis.size
 
+    # arithmetic roofs of this GPU (FMA throughput), for the FP64 kernels
+    alu = {}
+    try:
+        alu = {"fp64_tflops": _lib.eig_profile_alu_peak(64), "fp32_tflops": _lib.eig_profile_alu_peak(32),
+               "how": "independent FMA chains over 8 CTAs x 256 threads per SM, best of two (FP32 as packed pairs)"}
+    except Exception as ex:  # measurement aid only
+        alu = {"error": str(ex)}
+
     # step inputs: fresh RHS per step, resident on the device
     nsteps = a.warmup + a.steps
     B1 = [torch.from_numpy(next_rhs(1)[0]).to(dev) for _ in range(nsteps)]
@@ -477,8 +488,10 @@ def main():
     rhs_per_step = 1 + k
     value = job_rate(world, a.steps, rhs_per_step, ms)
     launches = int(sum(v["launches"] for v in prof.values()))
-    # dominant kernel roofline (HBM-bound stencil)
-    kern = max((n for n in prof if n.startswith("dslash")), key=lambda n: prof[n]["ms"])
+    # roofline of the dominant kernel: the one with the most device time in the timed
+    # region, whatever it is; every kernel of the path is HBM-bound at this size except
+    # the FP64 / double-float stencils (arithmetic), reported against the FMA roofs below
+    kern = max(prof, key=lambda n: prof[n]["ms"])
     kp = prof[kern]
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(peaks_path):
@@ -508,9 +521,18 @@ def main():
                 "variant": kvar, "link_reals": klinks,
                 "algorithmic_bytes_per_launch": kp["bytes"] / kp["launches"],
                 "avg_launch_ms": kp["ms"] / kp["launches"], "launches": kp["launches"]}
-    kernels = {n: {"launches": v["launches"], "ms": round(v["ms"], 3),
-                   "GBps": (v["bytes"] / (v["ms"] / 1e3) / 1e9) if v["ms"] > 0 else None}
-               for n, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}
+    kernels = {}
+    for n, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"]):
+        gbs = (v["bytes"] / (v["ms"] / 1e3) / 1e9) if v["ms"] > 0 else None
+        e = {"launches": v["launches"], "ms": round(v["ms"], 3), "GBps": gbs,
+             "frac_of_hbm": (gbs / peak) if gbs else None}
+        # FP64 stencils: ~1320 flop per site and RHS for one M (spin-projected count)
+        if n.startswith("dslash_") and "f64" in n and v["ms"] > 0 and alu.get("fp64_tflops"):
+            kk_ = int(n.rsplit("_k", 1)[1]) if "_k" in n else 1
+            tf = 1320.0 * V * kk_ * v["launches"] / (v["ms"] / 1e3) / 1e12
+            e["fp64_tflops"] = tf
+            e["frac_of_fp64_fma"] = tf / alu["fp64_tflops"]
+        kernels[n] = e
 
     # --- end to end: same steps with pinned host buffers -----------------------------
     e2e = None
@@ -529,6 +551,61 @@ def main():
         bytes_out = (1 + k) * V * 12 * 16
         e2e = {"value": world * a.steps * rhs_per_step / e2e_s, "unit": UNIT, "h2d_bytes_per_step": bytes_in,
                "d2h_bytes_per_step": bytes_out}
+
+    # --- what each part of the method buys on this GPU (one call each, synchronised) ----
+    def timed(fn):
+        torch.cuda.synchronize()
+        t0_ = time.perf_counter()
+        out_ = fn()
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0_, out_
+
+    arms = {}
+    if not a.no_plain:
+        bk, xk0 = Bk[0], torch.zeros_like(Bk[0])
+        dt, sts = timed(lambda: op.initcg_solve(bk, xk0, a.tol, a.restart_tol, basis=basis, k=k))
+        arms[f"deflated_initcg_fp32_k{k}"] = {"value": k / dt, "unit": UNIT,
+                                              "iters_mean": float(np.mean([q["iters"] for q in sts]))}
+        xk0 = torch.zeros_like(Bk[0])
+        dt, sts = timed(lambda: op.initcg_solve(bk, xk0, a.tol, k=k, max_iter=20000))
+        arms[f"plain_cg_fp32_k{k}"] = {"value": k / dt, "unit": UNIT,
+                                       "iters_mean": float(np.mean([q["iters"] for q in sts]))}
+        b1, x10 = B1[0], torch.zeros_like(B1[0])
+        dt, sts = timed(lambda: op.initcg_solve(b1, x10, a.tol, k=1, max_iter=20000))
+        arms["plain_cg_fp32_k1"] = {"value": 1 / dt, "unit": UNIT, "iters_mean": float(sts[0]["iters"])}
+        x10 = torch.zeros_like(B1[0])
+        dt, sts = timed(lambda: op.initcg_solve(b1, x10, a.tol, a.restart_tol, basis=basis, k=1))
+        arms["deflated_initcg_fp32_k1"] = {"value": 1 / dt, "unit": UNIT, "iters_mean": float(sts[0]["iters"])}
+
+    # --- serving: Poisson single-RHS requests on this operator and basis --------------
+    serve = None
+    if not a.no_serve and rank == 0 and arms:
+        from paper_0707_0131_gb300 import serving
+
+        spec = serving.OpSpec(key=a.lattice, dims=dims, m_q=m_q, gauge=gauge, prec=a.prec, max_rhs=k, nev=a.nev,
+                              m=a.m, basis_max=l0, tol=a.tol, restart_tol=a.restart_tol, prebuilt=(op, basis))
+        srv = serving.Server([spec], hbm_budget_bytes=a.budget_gb * 1e9)
+        cap = arms[f"deflated_initcg_fp32_k{k}"]["value"]
+        rate = 0.8 * cap
+        arrivals = serving.poisson_arrivals(rate, a.serve_requests, 105)
+        reqs = [next_rhs(1)[0].reshape(-1) for _ in range(a.serve_requests)]
+        futs = []
+        t0 = time.perf_counter()
+        for i, ta in enumerate(arrivals):
+            now = time.perf_counter() - t0
+            if ta > now:
+                time.sleep(ta - now)
+            futs.append(srv.submit(spec.key, reqs[i]))
+        res = [f.result() for f in futs]
+        wall = time.perf_counter() - t0
+        pct = srv.percentiles()
+        serve = {"value": len(res) / wall, "unit": UNIT, "p50_ms": pct["p50_ms"], "p99_ms": pct["p99_ms"],
+                 "requests": len(res), "arrival_rate_per_s": rate,
+                 "capacity_per_s": cap, "batch_histogram": srv.batch_histogram(),
+                 "max_true_rel_res": float(max(r["stats"]["true_rel_res"] for r in res)),
+                 "workload": f"Poisson arrivals at 0.8 x the k={k} deflated init-CG rate, one RHS per request, "
+                             f"continuous batching into init-CG calls of <= {k} RHS on the resident {l0}-vector basis"}
+        srv.close()
 
     # --- plain FP64 eigCG on the same GPU ---------------------------------------------
     plain = None
@@ -566,7 +643,9 @@ def main():
                           f"double-float residual replacements (delta {a.reliable_delta}), fp64 final residual", "l2": "inputs larger than L2 (each field >= 85 MB)",
                           "parallelism": f"replicas{world}"},
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-               "clocks": clk, "plain_fp64_eigcg": plain,
+               "clocks": clk, "p50_ms": serve["p50_ms"] if serve else None,
+               "p99_ms": serve["p99_ms"] if serve else None, "serving": serve, "arms": arms, "alu_peaks": alu,
+               "plain_fp64_eigcg": plain,
                "vs_plain_fp64_eigcg": (value / world / plain["value"]) if plain else None,
                "iters_per_rhs": {"eigcg_mean": float(np.mean(iters["eigcg"])),
                                  "initcg_mean": float(np.mean(iters["initcg"])),

@@ -234,22 +234,31 @@ typedef struct {
 eig_status eig_profile_enable(int on);
 eig_status eig_profile_reset(void);
 eig_status eig_profile_read(eig_kernel_stat *out, int max, int *n);
+/* Measured arithmetic roof of this GPU (measurement aid, no counterpart in the paper):
+ * fused multiply-add throughput in TFLOP/s for prec 64 (FP64) or 32 (FP32, packed
+ * pairs), from independent FMA chains over a grid that fills every SM, best of two
+ * timed launches on `stream` (synchronised).  The reference for kernels bound by
+ * arithmetic rather than memory.  Errors: EIG_ERR_ARG, EIG_ERR_CUDA. */
+eig_status eig_profile_alu_peak(int prec, double *tflops, void *stream);
 
 /* Allocation-free M, M^H or A = M^H M (which 0, 1, 2) on one FP64 RHS.  The paper
  * has no counterpart: this entry point exists for callers that may not allocate
- * device memory during the call (work inside a stream capture, memory owned by
- * another allocator, a device already reserved in full), which eig_op_apply cannot
- * serve because an op handle allocates its own buffers.
+ * device memory (memory owned by another allocator or pool that forbids cudaMalloc,
+ * a device already reserved in full), which eig_op_apply cannot serve because an op
+ * handle allocates its own buffers.  It calls no allocating routine.
  * gauge ([V][4][3][3] complex), in and out ([V][4][3] complex): DEVICE pointers in
- * the natural layout above, owned by the caller; in and out must not overlap.
+ * the natural layout above, owned by the caller, in the memory of the current device
+ * (or managed memory); out must not overlap in or gauge.
  * dims: each >= 2, Lx*Ly*Lz*Lt <= 65536 sites (EIG_ERR_BUDGET beyond).
  * A keeps its intermediate M in in a static device array of 65536 sites (12.6 MB)
- * shared by every call: it holds the last call's data (nothing in it needs to start
- * at zero), and calls that overlap on the GPU race on it.  The first call on each
- * device (with that device current) looks up the array's address and caches it;
- * make that call before any stream capture.  Asynchronous on `stream`.
- * Errors: EIG_ERR_ARG (null or host pointers, bad which/dims), EIG_ERR_BUDGET,
- * EIG_ERR_CUDA. */
+ * that every GPU loading the library holds until the process exits.  Every call
+ * shares it: it holds the last call's data (nothing in it needs to start at zero),
+ * and calls that overlap on the GPU race on it.  The first call on each device
+ * (with that device current) looks up the array's address and caches it; make that
+ * call before any stream capture (a first call on a capturing stream returns
+ * EIG_ERR_CUDA).  Asynchronous on `stream`.
+ * Errors: EIG_ERR_ARG (null pointers, host or other-device pointers, overlapping
+ * buffers, bad which/dims), EIG_ERR_BUDGET, EIG_ERR_CUDA. */
 eig_status eig_wilson_apply_noalloc(const double *gauge, const int dims[4], double m_q, int which, const double *in,
                                     double *out, void *stream);
 

@@ -3,6 +3,7 @@
 // updates, norms, and the p update of Fig. 1 step 9 fused with the eigCG window
 // append of Fig. 1 step 11.13 (V(:, i) = z / sqrt(rho), z = r for P = I).
 // All of them are HBM-bound streaming kernels over the chunk-major field layout.
+#include <string>
 #include <cstring>
 
 #include "kernels.cuh"
@@ -429,8 +430,10 @@ __global__ void k_pupdate(FieldView r, FieldView p, FieldView x, int first, cons
 
 cudaError_t launch_pupdate(Field r, Field p, Field x, bool first, CGScalars *st, Field v_append, cudaStream_t s) {
     const int app = v_append.v.data != nullptr;
-    ProfScope prof("pupdate", (double)r.v.V * r.v.k * ((first ? 2.0 : 3.0) * spb(r.prec) + (first ? 0.0 : 2.0 * spb(x.prec))) +
-                                  (app ? (double)r.v.V * spb(v_append.prec) : 0.0), s);
+    // per batch width, like the stencils: k = 1 fields (85 MB at 24^3x64) partly stay in L2
+    const std::string pname = r.v.k > 1 ? "pupdate_k" + std::to_string(r.v.k) : std::string("pupdate");
+    ProfScope prof(pname.c_str(), (double)r.v.V * r.v.k * ((first ? 2.0 : 3.0) * spb(r.prec) + (first ? 0.0 : 2.0 * spb(x.prec))) +
+                                      (app ? (double)r.v.V * spb(v_append.prec) : 0.0), s);
     const int B = 128;
     const int G = stream_grid(r.v.V * r.v.k, B);
     if (app && v_append.prec != x.prec) return cudaErrorInvalidValue;

@@ -19,6 +19,7 @@
 #include <cmath>
 #include <complex>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <mutex>
@@ -53,6 +54,11 @@ struct DevBuf {
     void alloc(size_t bytes) {
         release();
         if (bytes == 0) return;
+        // test hook (EIG_TEST_ALLOC_LIMIT=<bytes>): a fake of a failing cudaMalloc for
+        // larger requests, so that the out-of-memory path runs without exhausting a GPU
+        if (const char *ev = getenv("EIG_TEST_ALLOC_LIMIT"))
+            if (bytes > std::strtoull(ev, nullptr, 10))
+                throw Error{EIG_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed (test limit)"};
         cudaError_t e = cudaMalloc(&p, bytes);
         if (e != cudaSuccess) {
             p = nullptr;
@@ -586,6 +592,25 @@ struct Solve {
         }
         return trig;
     }
+    // Iterations until the next host check.  From the decay of rho over the iterations
+    // since the last check, the last active RHS is predicted to converge in n more
+    // iterations: the next check comes after min(n, CHECK) iterations (at least one), so
+    // that near convergence no iterations are launched for RHS that have stopped.
+    // Needs the history read up to j.
+    int iterations_to_next_check() const {
+        if (j < 2) return CHECK;
+        const int j0 = std::max(1, j - CHECK);
+        const double *r_ = hr();
+        double worst = 0.0;
+        for (int q = 0; q < k; q++) {
+            if (!sth[q].active) continue;
+            const double now = r_[(size_t)j * k + q], then = r_[(size_t)j0 * k + q];
+            if (!(now > 0.0) || !(then > now) || !(sth[q].target > 0.0)) return CHECK;
+            const double rate = std::log(now / then) / (j - j0);  // < 0
+            worst = std::max(worst, std::log(sth[q].target / now) / rate);
+        }
+        return (int)std::min<double>(CHECK, std::max(1.0, std::floor(worst)));
+    }
     void reliable_update() {
         true_residual(true, false);
         read_scalars();
@@ -700,9 +725,10 @@ static bool cg_run(Solve &sv, int max_iter, Window *w, eig_op_s *op) {
     cudaStream_t s = sv.s;
     const int k = sv.k;
     int since = CHECK;  // force a check at the start
+    int next_check = CHECK;
     while (true) {
         const bool restart_now = w && w->i == w->m;
-        if (since >= CHECK || restart_now || sv.j >= max_iter) {
+        if (since >= next_check || restart_now || sv.j >= max_iter) {
             sv.read_scalars();
             bool any = false;
             for (int q = 0; q < k; q++) any = any || sv.sth[q].active;
@@ -725,8 +751,10 @@ static bool cg_run(Solve &sv, int max_iter, Window *w, eig_op_s *op) {
             }
             sv.j_checked = sv.j;
             since = 0;
+            next_check = sv.iterations_to_next_check();
         }
-        if (!w && !sv.sp && since == 0 && sv.j >= 1 && sv.j + CHECK <= max_iter && cg_graphs_enabled()) {
+        if (!w && !sv.sp && since == 0 && next_check == CHECK && sv.j >= 1 && sv.j + CHECK <= max_iter &&
+            cg_graphs_enabled()) {
             // CHECK plain iterations as one replayed CUDA graph
             cudaGraphExec_t g = cg_graph(sv, op);
             *op->jbase_h.as<int>() = sv.j;
@@ -1214,6 +1242,13 @@ eig_status eig_profile_read(eig_kernel_stat *out, int max, int *n) {
     ARG_CHECK(n, "null argument");
     static_assert(sizeof(eig_kernel_stat) == sizeof(eig::KernelStat), "layout");
     *n = eig::prof_read(reinterpret_cast<eig::KernelStat *>(out), out ? max : 0);
+    API_END
+}
+
+eig_status eig_profile_alu_peak(int prec, double *tflops, void *stream) {
+    API_BEGIN
+    ARG_CHECK(tflops && (prec == 64 || prec == 32), "prec must be 64 or 32, tflops non-null");
+    CUDA_CK(eig::alu_peak(prec, tflops, (cudaStream_t)stream));
     API_END
 }
 
@@ -1756,11 +1791,18 @@ eig_status eig_initcg_solve(eig_op op, eig_basis basis, const double *b, double 
     int restarts = 0;
     bool ok = true;
     int rounds = 0;
+    // per-RHS iterations of phase 1 and the global iteration index phase 2 starts from:
+    // a RHS's count is its own phase-1 count plus the phase-2 iterations it took part in
+    // (the batch runs on after a RHS has reached restart_tol, and graph replays issue
+    // iterations past convergence)
+    int j1 = 0;
+    std::vector<int> it1(k, 0);
     if (defl && restart_tol > tol) {
         // phase 1: CG to restart_tol, then re-deflate from the current x (Sec. 5.3)
         sv.start(restart_tol);
         ok = cg_run(sv, max_iter, nullptr, op);
-        const int j1 = sv.j;
+        j1 = sv.j;
+        for (int q = 0; q < k; q++) it1[q] = sv.sth[q].iters;
         std::vector<int> rel1 = sv.reliable;
         if (ok) {
             sv.true_residual(false, false);  // x64 += x_lo; r64 = b - A x64
@@ -1788,7 +1830,7 @@ eig_status eig_initcg_solve(eig_op op, eig_basis basis, const double *b, double 
     if (stats) {
         for (int q = 0; q < k; q++) {
             eig_stats &st = stats[q];
-            st.iters = sv.sth[q].iters;
+            st.iters = restarts ? it1[q] + (sv.sth[q].iters - j1) : sv.sth[q].iters;
             st.restarts = restarts;
             st.reliable_updates = sv.reliable[q];
             const double bn2 = sv.sth[q].target / (tol * tol);

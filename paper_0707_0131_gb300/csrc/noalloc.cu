@@ -1,27 +1,26 @@
 // Allocation-free application of the Wilson operator (FP64, one RHS).
 //
-// Who needs it: callers that may not allocate device memory during the call --
-// code that runs while a stream is being captured into a CUDA graph (an
-// allocation there is either illegal or becomes part of the graph), applications
-// whose device memory belongs to another allocator or pool that forbids
-// cudaMalloc, and processes that have already reserved nearly all of the device.
-// eig_op_apply serves none of them: an op handle owns device buffers (the gauge
-// field in the library's own layout, staging for natural-layout vectors) that it
-// allocates when created.  eig_wilson_apply_noalloc works on caller-owned device
+// Who needs it: callers that may not allocate device memory -- applications whose
+// device memory belongs to another allocator or pool that forbids cudaMalloc, and
+// processes that have already reserved nearly all of the device for themselves.
+// eig_op_apply serves neither: an op handle owns device buffers (the gauge field in
+// the library's own layout, staging for natural-layout vectors) that it allocates
+// when it is created.  eig_wilson_apply_noalloc works on caller-owned device
 // buffers in the natural layout of eigcg.h and allocates nothing.
 //
 // Scratch: A = M^H M needs the intermediate M x.  It lives in g_noalloc_scratch,
 // a file-scope device array sized for NOALLOC_MAX_SITES lattice sites of one FP64
 // spinor (65536 * 12 complex doubles = 12.6 MB, present on every device that
-// loads this module).  Every call shares it and it keeps the contents of the last
-// call; the intermediate is written in full before it is read, so nothing in it
-// has to start at zero.  Calls that overlap on the GPU (different streams or
-// host threads at the same time) race on it and must be serialised by the caller.
+// loads this module until the process exits).  Every call shares it and it keeps
+// the contents of the last call; the intermediate is written in full before it is
+// read, so nothing in it has to start at zero.  Calls that overlap on the GPU
+// (different streams or host threads at the same time) race on it and must be
+// serialised by the caller.
 //
 // Set-up: the array's host-side name is not a device address.  The first call on
 // each device, with that device current, looks the address up once with
 // cudaGetSymbolAddress and caches it; that first call should come before any
-// stream capture starts.
+// stream capture starts (a first call on a capturing stream is refused).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
@@ -179,20 +178,28 @@ eig_status na_fail(eig_status st, const char *msg) {
     return st;
 }
 
-// true if [p, p + bytes) lies inside one device allocation of this process
-bool device_range_ok(const void *p, size_t bytes) {
+// true if [p, p + bytes) lies inside one device allocation of this process that the
+// current device `dev` can address: device memory of `dev` itself, or managed memory
+bool device_range_ok(const void *p, size_t bytes, int dev) {
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
     if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) return false;
+    if (at.type == cudaMemoryTypeDevice && at.device != dev) return false;  // another GPU's memory
     if (!g_range) return true;  // no range query available: the type check only
     CUdeviceptr base = 0;
     size_t size = 0;
     if (g_range(&base, &size, (CUdeviceptr)(uintptr_t)p) != CUDA_SUCCESS) return false;
     const uintptr_t lo = (uintptr_t)p, b = (uintptr_t)base;
     return lo >= b && lo - b + bytes <= size;
+}
+
+// true if the byte ranges [a, a + na) and [b, b + nb) share a byte
+bool overlaps(const void *a, size_t na, const void *b, size_t nb) {
+    const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+    return x < y + nb && y < x + na;
 }
 
 }  // namespace
@@ -218,10 +225,19 @@ extern "C" eig_status eig_wilson_apply_noalloc(const double *gauge, const int di
         cudaGetLastError();
         return na_fail(EIG_ERR_CUDA, "eig_wilson_apply_noalloc: no usable current device");
     }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
     double2 *scratch = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_na_mu);
         if (!g_na_ptr[dev]) {
+            // the one-time set-up makes runtime calls that do not belong inside a capture
+            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+            if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+                cudaGetLastError();
+                return na_fail(EIG_ERR_CUDA,
+                               "eig_wilson_apply_noalloc: the first call on a device sets up the scratch "
+                               "address and must not run on a capturing stream; call it once before capture");
+            }
             void *p = nullptr;
             const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
             if (e != cudaSuccess || !p) {
@@ -242,10 +258,13 @@ extern "C" eig_status eig_wilson_apply_noalloc(const double *gauge, const int di
         scratch = g_na_ptr[dev];
     }
     const size_t fbytes = (size_t)V * 12 * sizeof(double2), gbytes = (size_t)V * 36 * sizeof(double2);
-    if (!device_range_ok(gauge, gbytes) || !device_range_ok(in, fbytes) || !device_range_ok(out, fbytes))
+    if (!device_range_ok(gauge, gbytes, dev) || !device_range_ok(in, fbytes, dev) || !device_range_ok(out, fbytes, dev))
         return na_fail(EIG_ERR_ARG,
-                       "eig_wilson_apply_noalloc: gauge, in and out must be device buffers of the full lattice");
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
+                       "eig_wilson_apply_noalloc: gauge, in and out must be buffers of the full lattice in the "
+                       "memory of the current device (or managed memory)");
+    // every thread reads neighbour spinors of `in` and the links while others write `out`
+    if (overlaps(in, fbytes, out, fbytes) || overlaps(gauge, gbytes, out, fbytes))
+        return na_fail(EIG_ERR_ARG, "eig_wilson_apply_noalloc: out must not overlap in or gauge");
     const double2 *g = reinterpret_cast<const double2 *>(gauge);
     const double2 *x = reinterpret_cast<const double2 *>(in);
     double2 *y = reinterpret_cast<double2 *>(out);

@@ -127,4 +127,72 @@ int prof_read(KernelStat *out, int max) {
     return n;
 }
 
+// ------------------------------------------------------------------------------------
+// Arithmetic roofs: FP64 and FP32 fused multiply-add throughput of this GPU, measured
+// with independent FMA chains (8 per thread, FP32 as packed pairs) over a grid that
+// fills every SM; the reference for kernels bound by arithmetic rather than HBM.
+// ------------------------------------------------------------------------------------
+namespace {
+__global__ void k_fma64_probe(double *out, int iters, double a, double b) {
+    double x[8];
+#pragma unroll
+    for (int j = 0; j < 8; j++) x[j] = threadIdx.x * 1e-3 + j;
+    for (int i = 0; i < iters; i++)
+#pragma unroll
+        for (int j = 0; j < 8; j++) x[j] = fma(x[j], a, b);
+    double sm = 0.0;
+#pragma unroll
+    for (int j = 0; j < 8; j++) sm += x[j];
+    if (sm == 1234.5) out[0] = sm;  // never true: keeps the chains alive
+}
+__global__ void k_fma32_probe(float *out, int iters, float a, float b) {
+    float2 x[8];
+    const float2 a2 = make_float2(a, a), b2 = make_float2(b, b);
+#pragma unroll
+    for (int j = 0; j < 8; j++) x[j] = make_float2(threadIdx.x * 1e-3f + j, j * 0.5f);
+    for (int i = 0; i < iters; i++)
+#pragma unroll
+        for (int j = 0; j < 8; j++) x[j] = __ffma2_rn(x[j], a2, b2);
+    float sm = 0.f;
+#pragma unroll
+    for (int j = 0; j < 8; j++) sm += x[j].x + x[j].y;
+    if (sm == 1234.5f) out[0] = sm;
+}
+}  // namespace
+
+cudaError_t alu_peak(int prec, double *tflops, cudaStream_t s) {
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int threads = 256, blocks = sms * 8;
+    const int iters = prec == 64 ? 512 : 16384;
+    void *buf = nullptr;
+    e = cudaMallocAsync(&buf, 16, s);
+    if (e != cudaSuccess) return e;
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    float best = 0.f;
+    for (int rep = 0; rep < 3; rep++) {
+        cudaEventRecord(a, s);
+        if (prec == 64) k_fma64_probe<<<blocks, threads, 0, s>>>((double *)buf, iters, 0.999999, 1e-7);
+        else k_fma32_probe<<<blocks, threads, 0, s>>>((float *)buf, iters, 0.999f, 1e-4f);
+        cudaEventRecord(b, s);
+        e = cudaEventSynchronize(b);
+        if (e != cudaSuccess) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        if (rep > 0 && (best == 0.f || ms < best)) best = ms;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaFreeAsync(buf, s);
+    if (e != cudaSuccess) return e;
+    // FMAs: threads * iters * 8 chains (x 2 lanes for the packed FP32 pairs); 2 flops each
+    const double fmas = (double)blocks * threads * iters * 8.0 * (prec == 64 ? 1.0 : 2.0);
+    *tflops = 2.0 * fmas / (best * 1e-3) / 1e12;
+    return cudaGetLastError();
+}
+
 }  // namespace eig

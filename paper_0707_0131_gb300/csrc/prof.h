@@ -41,5 +41,7 @@ void prof_enable(bool on);
 void prof_reset();
 // Synchronises the device, folds pending event pairs into the totals.
 int prof_read(KernelStat *out, int max);
+// Measured FMA throughput (TFLOP/s) in FP64 (prec 64) or FP32 (prec 32); synchronises s.
+cudaError_t alu_peak(int prec, double *tflops, cudaStream_t s);
 
 }  // namespace eig

@@ -68,14 +68,14 @@ __device__ __forceinline__ uint64_t gtimer() {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
-// bounded wait: gives up after WAIT_NS nanoseconds of wall time
-__device__ __noinline__ bool mbar_wait(uint64_t *b, unsigned phase) {
+// bounded wait: gives up after limit_ns nanoseconds of wall time (WAIT_NS by default)
+__device__ __noinline__ bool mbar_wait(uint64_t *b, unsigned phase, uint64_t limit_ns = WAIT_NS) {
     if (mbar_try(b, phase)) return true;
     const uint64_t t0 = gtimer();
     for (;;) {
         for (int i = 0; i < 256; i++)
             if (mbar_try(b, phase)) return true;
-        if (gtimer() - t0 > WAIT_NS) return false;
+        if (gtimer() - t0 > limit_ns) return false;
     }
 }
 
@@ -139,6 +139,10 @@ struct TcArgs {
     int chunk;         // K tiles per CTA
     double *partials;  // [grid][MT * 128][N]
     int *err;
+    // test hook (EIG_TEST_INJECT_WAIT): CTA 0 first waits, for at most inject_ns, on an
+    // mbarrier that nothing arrives on, then takes the give-up path before any copy is
+    // issued, so that the error status can be exercised without a real stall
+    uint64_t inject_ns;
 };
 
 // s += x in double-float (hi, lo) with Knuth's TwoSum (exact error of the FP32 sum)
@@ -197,7 +201,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_ahb(const __grid_constant_
     constexpr uint32_t RCOLS = MT * N;
     constexpr uint32_t NCOLS = NREG * RCOLS <= 32 ? 32 : (NREG * RCOLS <= 64 ? 64 : (NREG * RCOLS <= 128 ? 128 : 256));
     __shared__ __align__(8) uint64_t raw_full[NS], split_done[NS], stage_free[NS], acc_full[NREG], acc_empty[NREG],
-        done;
+        done, never;
     __shared__ uint32_t tmem_base;
     __shared__ volatile int abort_flag;
     __shared__ int n_issued, n_consumed;
@@ -216,6 +220,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_ahb(const __grid_constant_
             mbar_init(&acc_empty[r], WORKERS);
         }
         mbar_init(&done, 1);
+        mbar_init(&never, 1);
         abort_flag = 0;
         n_issued = 0;
         n_consumed = 0;
@@ -239,6 +244,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_ahb(const __grid_constant_
         atomicExch(a.err, code);
         abort_flag = 1;
     };
+    if (a.inject_ns && blockIdx.x == 0) {  // block-uniform
+        if (t == 0 && !mbar_wait(&never, 0, a.inject_ns)) fail(7);
+        __syncthreads();
+    }
 
     if (warp == 0) {
         // ---------------- producer: TMA loads of the A tiles ----------------
@@ -799,6 +808,9 @@ cudaError_t launch_tc_ahb(const ColSet &A, const ColSet &B, long nrows, double *
     a.ktiles = (int)((2 * nrows + KT - 1) / KT);
     a.partials = partials;
     a.err = err;
+    a.inject_ns = 0;
+    if (const char *ev = getenv("EIG_TEST_INJECT_WAIT"))
+        if (ev[0] == '1') a.inject_ns = 5000000ull;  // 5 ms
     int grid = 0;
     tc_grid(a.ktiles, &a.chunk, &grid);
     const size_t stage = 2 * MT * (size_t)(TM * KT * 4) + 2 * (size_t)((N + 7) / 8) * 1024;

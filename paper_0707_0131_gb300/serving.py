@@ -51,6 +51,9 @@ class OpSpec:
     # longer pays; 0 grows the basis to basis_max
     expected_requests: int = 0
     eigcg_overhead: float = 1.2
+    # an operator and basis that already exist (Op, Basis): served as they are, never
+    # closed by the server; its footprint still counts against the budget
+    prebuilt: tuple = None
 
     def footprint(self) -> int:
         """Device bytes of an active operator: links, workspace, window, basis."""
@@ -95,15 +98,19 @@ class _Worker:
 
         self.stream = torch.cuda.Stream()
         s = self.spec
-        self.op = Op(s.gauge, s.dims, s.m_q, prec=s.prec, max_rhs=s.max_rhs)
-        self.basis = Basis(self.op, s.basis_max + s.nev)
+        if s.prebuilt is not None:
+            self.op, self.basis = s.prebuilt
+        else:
+            self.op = Op(s.gauge, s.dims, s.m_q, prec=s.prec, max_rhs=s.max_rhs)
+            self.basis = Basis(self.op, s.basis_max + s.nev)
         self.active = True
 
     def retire(self):
-        if self.basis is not None:
-            self.basis.close()
-        if self.op is not None:
-            self.op.close()
+        if self.spec.prebuilt is None:
+            if self.basis is not None:
+                self.basis.close()
+            if self.op is not None:
+                self.op.close()
         self.op = self.basis = None
         self.active = False
 
@@ -226,6 +233,12 @@ class Server:
     def percentiles(self):
         a = np.array(self.latencies)
         return {"p50_ms": float(np.percentile(a, 50)), "p99_ms": float(np.percentile(a, 99)), "n": int(a.size)}
+
+    def batch_histogram(self):
+        """{batch size: number of requests served in batches of that size}."""
+        with self.cv:
+            sizes = [rec[4] for rec in self.records]
+        return {int(b): int(sum(1 for x in sizes if x == b)) for b in sorted(set(sizes))}
 
     def close(self):
         for w in self.workers.values():

@@ -4,6 +4,15 @@ Bars (stated with the method): FP64 true residual ||b - A x|| / ||b|| <= tol
 recomputed by the oracle; iteration counts within 10% of the oracle's; converged
 Ritz values within 1e-6 relative; the Galerkin condition of Eq. 1 holds for the
 GPU's own basis.  Mixed precision reaches tol through reliable updates.
+
+Which Ritz values are compared: a Ritz pair (theta, v) of a Hermitian A with residual
+rho = ||A v - theta v|| (||v|| = 1) lies within rho of an eigenvalue (Bauer-Fike) and,
+when the rest of the spectrum is at least `gap` away, within rho^2 / gap of it
+(Kato-Temple).  A pair converged to rho <= sqrt(eps) ||A|| is therefore fixed by A
+alone, to far below 1e-6 relative, and two runs that both converged it must agree at
+1e-6.  Unconverged Ritz values depend on the rounding history of the Lanczos
+process, so for them only the bounds that hold for any Rayleigh-Ritz pair are
+checked (Bauer-Fike, and interlacing theta_i >= lambda_i).
 """
 import json
 import os
@@ -49,6 +58,27 @@ def _close_iters(a, b, frac=0.1):
     return abs(a - b) <= max(1, frac * b)
 
 
+SQRT_EPS64 = float(np.sqrt(np.finfo(np.float64).eps))
+
+
+def _check_converged_match(th_g, th_o, rn_o, normA, min_pairs, rel=1e-6):
+    """Every oracle pair converged to rho <= sqrt(eps64) ||A|| (at least min_pairs of
+    them) has a GPU Ritz value within rel."""
+    conv = np.flatnonzero(np.asarray(rn_o) <= SQRT_EPS64 * normA)
+    assert len(conv) >= min_pairs, (len(conv), np.asarray(rn_o) / normA)
+    th_g = np.asarray(th_g)
+    for c in conv:
+        d = float(np.min(np.abs(th_g - th_o[c])) / th_o[c])
+        assert d < rel, (int(c), th_o[c], d)
+    return len(conv)
+
+
+def _check_bauer_fike(th, rn, lam, slack=1e-9):
+    """Each Ritz value lies within its residual norm of an eigenvalue of A."""
+    for t, r in zip(th, rn):
+        assert np.min(np.abs(lam - t)) <= r * (1 + 1e-6) + slack, (t, r)
+
+
 def test_cg_parity_fp64(api, small):
     dims, m_q, gauge, W, bs = small
     op = api.Op(gauge, dims, m_q, prec=64)
@@ -74,15 +104,15 @@ def test_eigcg_parity_fp64(api, small):
     assert _true_res(W, x, bs[0]) <= 1e-10
     basis.grow()
     theta, res = basis.ritz()
-    theta = np.sort(theta)
-    # The bottom of this spectrum is clustered (gaps ~1e-5 ||A||), so no Ritz pair is
-    # converged when CG stops; GPU and oracle run the same Lanczos process, and their
-    # Ritz values agree to the accuracy with which each is determined.
-    rel = np.abs(theta[:8] - o["ritz"][:8]) / o["ritz"][:8]
-    assert np.all(rel[:2] < 1e-6) and np.all(rel < 1e-4), rel
-    # all Ritz values lie above the exact eigenvalues
+    order = np.argsort(theta)
+    theta, res = theta[order], res[order]
+    # No Ritz pair of this clustered spectrum (gaps ~1e-5 ||A||) converges before CG
+    # stops (oracle residuals 3e-5 .. 3e-4 ||A||), so the values themselves are set by
+    # the rounding history; the bounds that hold for every Rayleigh-Ritz pair are checked
+    # (converged pairs are compared in the Incremental eigCG and free-field tests).
     lam = np.linalg.eigvalsh(W.dense("A"))
-    assert np.all(np.sort(theta) >= lam[: len(theta)] - 1e-9)
+    assert np.all(theta >= lam[: len(theta)] - 1e-9)
+    _check_bauer_fike(theta, res, lam)
     basis.close()
     op.close()
 
@@ -134,14 +164,19 @@ def test_incremental_and_initcg_parity_fp64(api, small):
     assert np.max(np.abs(U.conj().T @ U - np.eye(l))) < 1e-10
     AU = np.stack([W.A(U[:, c]) for c in range(l)], axis=1)
     assert np.max(np.abs(H - U.conj().T @ AU)) < 1e-10 * 64
-    # Rayleigh-Ritz on the GPU basis against the oracle's on its own basis; the bottom
-    # of this spectrum is clustered, so compare to the accuracy each run determines
+    # Rayleigh-Ritz on the GPU basis against the oracle's on its own basis: after four
+    # RHS the lowest pairs have converged in both (oracle residuals ~1e-9 ||A||)
     th_g, rn_g = basis.ritz()
     th_o, rn_o, _ = solvers.basis_ritz(W, U0, H0)
-    rel = np.abs(th_g[:8] - th_o[:8]) / th_o[:8]
-    assert np.all(rel[:2] < 1e-6) and np.all(rel < 1e-4), (rel, rn_o[:8])
     lam = np.linalg.eigvalsh(W.dense("A"))
+    normA = lam[-1]
+    _check_converged_match(th_g, th_o, rn_o, normA, min_pairs=8)
     assert np.all(th_g >= lam[: len(th_g)] - 1e-9)
+    _check_bauer_fike(th_g, rn_g, lam)
+    # the GPU's own converged pairs sit on eigenvalues of A at 1e-6
+    for t, r in zip(th_g, rn_g):
+        if r <= SQRT_EPS64 * normA:
+            assert np.min(np.abs(lam - t)) / t < 1e-6, (t, r)
     # init-CG, 4 RHS in one batch, restarted once at 1e-5
     B = np.stack(bs[4:8])
     X = np.zeros_like(B)
@@ -149,7 +184,7 @@ def test_incremental_and_initcg_parity_fp64(api, small):
     for r in range(4):
         o = solvers.initcg(W, U, H, bs[4 + r], tol=1e-10, restart_tol=1e-5)
         assert sts[r]["restarts"] == 1
-        assert _close_iters(sts[r]["iters"], o["iters"], 0.15), (r, sts[r]["iters"], o["iters"])
+        assert _close_iters(sts[r]["iters"], o["iters"]), (r, sts[r]["iters"], o["iters"])
         assert _true_res(W, X[r], bs[4 + r]) <= 1e-10
     plain = solvers.cg(W, bs[4], tol=1e-10)
     assert sts[0]["iters"] < plain["iters"]
@@ -196,20 +231,65 @@ def test_mixed_precision_reaches_1e8(api, prec, frac):
     assert _true_res(W, x, b) <= 1e-8
     assert st["reliable_updates"] >= 1
     assert _close_iters(st["iters"], o["iters"], frac), (st["iters"], o["iters"])
-    # eigCG in mixed precision: same residual bar, Ritz values near the FP64 ones
+    # eigCG in mixed precision: same residual bar.  No Ritz pair converges on this
+    # problem in one solve (oracle residuals >= 3e-5 ||A||), so the GPU's Rayleigh-Ritz
+    # is checked on its own basis: the oracle's Ritz values of span(U_gpu) (U in
+    # FP64, H = U^H A U recomputed by the oracle) against basis.ritz()
     basis = api.Basis(op, 16)
     x2 = np.zeros_like(b)
     st2 = op.eigcg_solve(b, x2, nev=8, m=40, tol=1e-8, basis=basis)
     assert _true_res(W, x2, b) <= 1e-8
     basis.grow()
     th, rn = basis.ritz()
-    oe = solvers.eigcg(W, b, nev=8, m=40, tol=1e-8)
-    # FP32: relative 1e-4; FP16 Lanczos vectors resolve eigenvalues only to a small
-    # multiple of eps_16 ||A|| (||A|| ~ 64 here), so its bar is absolute
-    if prec == 32:
-        assert abs(th[0] - oe["ritz"][0]) / oe["ritz"][0] < 1e-4
-    else:
-        assert abs(th[0] - oe["ritz"][0]) < 1e-5 * 64
+    U = basis.vectors()
+    AU = np.stack([W.A(U[:, c]) for c in range(U.shape[1])], axis=1)
+    H_o = U.conj().T @ AU
+    th_o, S_o = np.linalg.eigh((H_o + H_o.conj().T) / 2)
+    order = np.argsort(th)
+    th, rn = th[order], rn[order]
+    assert np.max(np.abs(th - th_o) / th_o) < 1e-6
+    # residual norms: the GPU forms its Ritz vectors U S in FP32 storage, which adds up to
+    # ~eps32 ||A|| to ||A x - theta x||
+    X = U @ S_o
+    rn_o = np.linalg.norm(AU @ S_o - X * th_o, axis=0)
+    normA = (8 + m_q) ** 2
+    assert np.all(np.abs(rn - rn_o) <= 1e-3 * rn_o + 8 * np.finfo(np.float32).eps * normA), (rn, rn_o)
+    op.close()
+
+
+def test_eigcg_fp32_converged_free_field(api):
+    """FP32 storage, free field on 4x6x8x10: the Ritz pairs that eigCG converges are
+    the closed-form levels at 1e-6.  A GPU pair is taken as converged when its own
+    residual rho bounds its distance to the level by rho^2 / gap <= 1e-7 theta
+    (Kato-Temple, gap to the next closed-form level)."""
+    import itertools
+
+    dims = (4, 6, 8, 10)
+    m = 0.1
+    ps = [2 * np.pi * np.arange(L) / L for L in dims]
+    lev = np.array(sorted({round((m + np.sum(1 - np.cos(p))) ** 2 + np.sum(np.sin(p) ** 2), 12)
+                           for p in map(np.array, itertools.product(*ps))}))
+    b = fx.make_rhs(dims, 5)[0].reshape(-1)
+    W = oracle.Wilson(dims, m, fx.unit_gauge(dims))
+    op = api.Op(fx.unit_gauge(dims), dims, m, prec=32)
+    basis = api.Basis(op, 8)
+    x = np.zeros_like(b)
+    st = op.eigcg_solve(b, x, nev=6, m=16, tol=1e-8, basis=basis)
+    assert st["restarts"] > 5
+    assert _true_res(W, x, b) <= 1e-8
+    o = solvers.eigcg(W, b, nev=6, m=16, tol=1e-8)
+    assert _close_iters(st["iters"], o["iters"]), (st["iters"], o["iters"])
+    basis.grow()
+    th, rn = basis.ritz()
+    n_conv = 0
+    for t, r in zip(th, rn):
+        i = int(np.argmin(np.abs(lev - t)))
+        gap = float(np.min(np.abs(np.delete(lev, i) - t)))
+        if r * r / gap <= 1e-7 * t:
+            n_conv += 1
+            assert abs(t - lev[i]) / lev[i] < 1e-6, (t, lev[i], r)
+    assert n_conv >= 3, (th, rn)
+    basis.close()
     op.close()
 
 

@@ -1,14 +1,18 @@
-"""The allocation-free entry point eig_wilson_apply_noalloc against eig_op_apply.
+"""The allocation-free entry point eig_wilson_apply_noalloc against eig_op_apply
+and the oracle.
 
-Both apply the same FP64 operator; the allocation-free one works on caller-owned
-device buffers with its intermediate in a static device array shared by all calls.
-Two calls in a row (the second one finds the first one's data in the array) must
-each match eig_op_apply within the FP64 matvec tolerance of the other tests.
-Argument errors are rejected on the host before anything reaches the GPU.
+It serves callers that may not allocate device memory (memory owned by another
+allocator, a device reserved in full).  Both entry points apply the same FP64
+operator; the allocation-free one works on caller-owned device buffers with its
+intermediate in a static device array shared by all calls.  Two calls in a row (the
+second one finds the first one's data in the array) must each match eig_op_apply
+and the FP64 oracle within the FP64 matvec tolerance of the other tests.  Argument
+errors are rejected on the host before anything reaches the GPU.
 """
 import numpy as np
 import pytest
 
+import oracle
 from paper_0707_0131_gb300 import _lib
 from paper_0707_0131_gb300 import fixtures as fx
 
@@ -31,6 +35,7 @@ def test_noalloc_matches_op_apply(dims):
     op = _lib.eig_op_create(gauge, dims, m_q, spinor_prec=64)
     d_gauge = torch.from_numpy(np.ascontiguousarray(gauge)).cuda()
     V = fx.volume(dims)
+    W = oracle.Wilson(dims, m_q, gauge)
     try:
         for call in range(2):
             psi = fx.make_rhs(dims, 42 + call, 1)[0]
@@ -45,6 +50,9 @@ def test_noalloc_matches_op_apply(dims):
                 assert out.shape == (V, 4, 3)
                 err = _relerr(out.reshape(-1), ref.reshape(-1))
                 assert err < TOL64, (call, which, err)
+                o = (W.M, W.Mdag, W.A)[which](psi.reshape(-1))
+                err_o = _relerr(out.reshape(-1), o)
+                assert err_o < TOL64, (call, which, err_o)
     finally:
         _lib.eig_op_destroy(op)
 
@@ -90,11 +98,11 @@ def test_noalloc_rejects_bad_arguments_on_the_host():
     with pytest.raises(_lib.EigError) as e:
         _lib.eig_wilson_apply_noalloc(g, (4, 4, 1, 4), 0.1, 0, v, v.copy())
     assert e.value.status == _lib.EIG_ERR_ARG
-    big = (32, 32, 32, 8)  # 262144 sites > 65536
-    with pytest.raises(_lib.EigError) as e:
-        _lib.eig_wilson_apply_noalloc(g, big, 0.1, 0, v, v.copy())
-    assert e.value.status == _lib.EIG_ERR_BUDGET
-    assert "65536" in _lib.eig_last_error()
+    for big in ((32, 32, 32, 8), (16, 16, 16, 17)):  # 262144 and 69632 sites > 65536
+        with pytest.raises(_lib.EigError) as e:
+            _lib.eig_wilson_apply_noalloc(g, big, 0.1, 0, v, v.copy())
+        assert e.value.status == _lib.EIG_ERR_BUDGET
+        assert "65536" in _lib.eig_last_error()
 
 
 @pytest.mark.gpu
@@ -111,3 +119,11 @@ def test_noalloc_rejects_host_buffers():
     with pytest.raises(_lib.EigError) as e:
         _lib.eig_wilson_apply_noalloc(g, dims, 0.1, 0, v, np.empty_like(v))
     assert e.value.status == _lib.EIG_ERR_ARG
+    # device buffers, but out overlapping in or the gauge field: refused before launch
+    d_g = torch.from_numpy(np.ascontiguousarray(g)).cuda()
+    d_v = torch.from_numpy(v).cuda()
+    for out in (d_v, d_g.view(-1)[: v.size].view(v.shape)):
+        with pytest.raises(_lib.EigError) as e:
+            _lib.eig_wilson_apply_noalloc(d_g, dims, 0.1, 2, d_v, out)
+        assert e.value.status == _lib.EIG_ERR_ARG
+        assert "overlap" in _lib.eig_last_error()
