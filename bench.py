@@ -510,7 +510,8 @@ def main():
     tfile = os.path.join(ROOT, "configs", "traffic.json")
     if os.path.exists(tfile):
         h = hashlib.sha1()
-        for f in ("dslash32.cuh", "dslash32.cu", "dslash32d_rb1.cu", "dslash32d_rb2.cu"):
+        for f in ("dslash32.cuh", "dslash32.cu", "dslash32d_rb1.cu", "dslash32d_rb2.cu", "dslash32pp.cuh",
+                  "dslash32p2.cu", "dslash32p3.cu"):
             h.update(open(os.path.join(ROOT, "paper_0707_0131_gb300", "csrc", f), "rb").read())
         for tj in json.load(open(tfile)).get(kern, []):
             if (tj.get("stencil_sha1") == h.hexdigest() and tj.get("variant") == kvar
@@ -639,7 +640,7 @@ def main():
                                       f"per step 1 eigCG({a.nev},{a.m}) + grow + k={k} batched init-CG, "
                                       f"basis {l0} FP32 vectors, tol {a.tol}, restart {a.restart_tol}",
                           "lattice": a.lattice, "k": k, "basis": l0, "storage": ("fp32 spinors, fp32 links (12- and 18-real resident, chosen per k by the autotuner), " if a.prec == 32 else
-                                     "fp16 spinors with one fp32 scale per site, fp16 12-real links, fp32 eigCG window and basis, ") +
+                                     "fp16 spinors with one fp32 scale per site and RHS, fp32 12-real links, fp32 eigCG window and basis, ") +
                           f"double-float residual replacements (delta {a.reliable_delta}), fp64 final residual", "l2": "inputs larger than L2 (each field >= 85 MB)",
                           "parallelism": f"replicas{world}"},
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,

@@ -58,7 +58,7 @@ typedef enum {
 /* Storage precision codes for spinor_prec. */
 #define EIG_PREC_F64 64  /* FP64 storage and arithmetic                                  */
 #define EIG_PREC_F32 32  /* FP32 storage and arithmetic, FP64 reductions                 */
-#define EIG_PREC_F16 16  /* FP16 storage with one FP32 scale per site, FP32 arithmetic   */
+#define EIG_PREC_F16 16  /* FP16 spinors, one FP32 scale per site; FP32 links and arithmetic */
 
 typedef struct eig_op_s *eig_op;
 typedef struct eig_basis_s *eig_basis;

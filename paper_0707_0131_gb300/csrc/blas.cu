@@ -506,6 +506,7 @@ __global__ void k_cg_init(CGScalars *st, int k, double tol2, double *h_beta) {
     st[r].beta = 0.0;
     st[r].pAp = 0.0;
     st[r].iters = 0;
+    st[r].nit = 0;
     st[r].x_pending = 0;
     if (h_beta) h_beta[k + r] = 0.0;  // beta_1 := 0
 }

@@ -316,6 +316,7 @@ __global__ void __launch_bounds__(128) k_dslash(const KArgs a) {
                     return;
                 }
                 st.iters = iter;
+                st.nit++;
                 st.rho_prev = st.rho;
                 st.rho = tot;
                 st.beta = tot / st.rho_prev;
@@ -456,7 +457,7 @@ static cudaError_t dispatch(const DslashCall &c, KArgs &a, int cap, cudaStream_t
             }
             break;
         case P16:
-            if (EPI != EPI_RESID && c.gformat == GF_F16_12) EIG_LAUNCH(__half, GF_F16_12);
+            if (EPI != EPI_RESID && c.gformat == GF_F32_12) EIG_LAUNCH(__half, GF_F32_12);
             break;
     }
 #undef EIG_LAUNCH

@@ -1,5 +1,6 @@
 // FP32-arithmetic Wilson stencil: the staged (cp.async) variants, the choice between
 // variants and the launchers.  Kernels and design notes: dslash32.cuh.
+#include <cstdint>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -23,20 +24,36 @@ std::unordered_map<const void *, int> g_occ32;
 //   6  as 4, with an L1 prefetch of the next hop           7  as 3, with the L1 prefetch
 //   8 + v (v = 2..7): direct variant v over the tiled site traversal (full lattice only;
 //   v itself where the lattice cannot be tiled)
+//  16  pipelined pair (dslash32pp.cuh): 2 adjacent RHS per thread, 256-bit loads, the
+//      next hop's loads in flight while the current one is computed, 2 blocks/SM
+//  17  as 16, 3 blocks/SM        18, 19: 16, 17 over the tiled site traversal
 // The fastest valid one is chosen per (volume, k, storage, link format) by
-// autotune_dslash32 and cached; EIG_DSLASH_VARIANT=0..15 in the environment forces one.
-constexpr int NVAR = 16;
+// autotune_dslash32 and cached; EIG_DSLASH_VARIANT=0..19 in the environment forces one.
+constexpr int NVAR = 20;
+
+bool is_pp(int v) { return v >= 16; }
+bool is_tiled(int v) { return (v >= 8 && v < 16) || v >= 18; }
 
 int variant_rb(int v) {
+    if (is_pp(v)) return 2;
     v &= 7;
     return (v == 1 || v == 4 || v == 5 || v == 6) ? 2 : 1;
 }
 
 bool variant_ok(int v, unsigned k, int gf) {
     if (v < 0 || v >= NVAR) return false;
-    if (v >= 8 && (v & 7) < 2) return false;  // tiling only for the direct variants
+    if (v >= 8 && v < 16 && (v & 7) < 2) return false;  // tiling only for the direct variants
     if (variant_rb(v) == 2 && (k < 2 || (k % 2) != 0)) return false;
     return true;
+}
+
+// the pipelined-pair variants load and store 32 bytes per thread: every field they touch
+// must start on a 32-byte boundary (scale arrays on an 8-byte one); they do not write the
+// single-RHS t_prev copy of eigCG
+bool pp_aligned(const K32 &a) {
+    const uintptr_t f = (uintptr_t)a.in | (uintptr_t)a.out | (uintptr_t)a.r | (uintptr_t)a.cen;
+    const uintptr_t sc = (uintptr_t)a.in_s | (uintptr_t)a.out_s | (uintptr_t)a.r_s | (uintptr_t)a.cen_s;
+    return (f & 31) == 0 && (sc & 7) == 0 && !a.save_t;
 }
 
 // Tiled traversal for a launch with rb RHS per thread: a tile of as many sites as a CTA
@@ -144,7 +161,12 @@ cudaError_t launch_rb(const K32 &a, int cap, cudaStream_t s) {
     const int v = variant_for(a, prec, GF);
     if (v <= 1) return launch_staged<S, GF, DAG, EPI>(variant_rb(v), a, cap, s);
     K32 b = a;
-    if (v >= 8) tile_setup(b, variant_rb(v));
+    if (is_tiled(v)) tile_setup(b, variant_rb(v));
+    if (is_pp(v)) {
+        if (!pp_aligned(b)) return d32_launch_direct_rb2(4, prec, GF, DAG, EPI, b, cap, s);
+        return (v == 16 || v == 18) ? d32_launch_pp2(prec, GF, DAG, EPI, b, cap, s)
+                                    : d32_launch_pp3(prec, GF, DAG, EPI, b, cap, s);
+    }
     if (variant_rb(v) == 1) return d32_launch_direct_rb1(v & 7, prec, GF, DAG, EPI, b, cap, s);
     return d32_launch_direct_rb2(v & 7, prec, GF, DAG, EPI, b, cap, s);
 }
@@ -157,7 +179,7 @@ cudaError_t dispatch32(const DslashCall &c, const K32 &a, int cap, cudaStream_t 
         if (c.gformat == GF_F32_12) EIG32(float, GF_F32_12);
         if (c.gformat == GF_F32_18) EIG32(float, GF_F32_18);
     } else if (c.in.prec == P16) {
-        if (c.gformat == GF_F16_12) EIG32(__half, GF_F16_12);
+        if (c.gformat == GF_F32_12) EIG32(__half, GF_F32_12);
     }
 #undef EIG32
     return cudaErrorInvalidValue;
@@ -285,7 +307,8 @@ cudaError_t autotune_dslash32(const DslashCall &c0, const void *const *gauge_alt
         for (int v = 0; v < NVAR; v++) {
             if (!variant_ok(v, a.k, c.gformat)) continue;
             K32 tb = a;
-            if (v >= 8 && !tile_setup(tb, variant_rb(v))) continue;  // same as v - 8 here
+            if (is_tiled(v) && !tile_setup(tb, variant_rb(v))) continue;  // same as the untiled one here
+            if (is_pp(v) && !pp_aligned(a)) continue;
             if (forced_variant() >= 0 && v != forced_variant()) continue;
             g_var_override = v;
             dispatch32<E_PLAIN>(c, a, 0, s);  // warm

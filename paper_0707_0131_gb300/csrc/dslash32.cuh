@@ -71,6 +71,10 @@ cudaError_t d32_launch_direct_rb1(int variant, int prec, int gf, bool dag, int e
                                   cudaStream_t s);
 cudaError_t d32_launch_direct_rb2(int variant, int prec, int gf, bool dag, int epi, const K32 &a, int cap,
                                   cudaStream_t s);
+// launchers of the pipelined-pair variants (dslash32p2.cu, dslash32p3.cu: 2 or 3 blocks
+// per SM; k >= 2, fields 32-byte aligned)
+cudaError_t d32_launch_pp2(int prec, int gf, bool dag, int epi, const K32 &a, int cap, cudaStream_t s);
+cudaError_t d32_launch_pp3(int prec, int gf, bool dag, int epi, const K32 &a, int cap, cudaStream_t s);
 // grid for a launch of `kern` (TPB threads, `smem` bytes of dynamic shared memory):
 // resident blocks per SM x SMs, no more blocks than `work` threads need, at most cap
 int d32_grid(const void *kern, long work, int cap, size_t smem);
@@ -701,6 +705,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_dslash32(const K32 a) {
                     return;
                 }
                 st.iters = iter;
+                st.nit++;
                 st.rho_prev = st.rho;
                 st.rho = tot;
                 st.beta = tot / st.rho_prev;
@@ -737,7 +742,7 @@ template <int RB, int MINB, int MODE>
 cudaError_t d32_direct(int prec, int gf, bool dag, int epi, const K32 &a, int cap, cudaStream_t s) {
     if (prec == 32 && gf == GF_F32_12) return d32_direct_fmt<RB, MINB, MODE, float, GF_F32_12>(dag, epi, a, cap, s);
     if (prec == 32 && gf == GF_F32_18) return d32_direct_fmt<RB, MINB, MODE, float, GF_F32_18>(dag, epi, a, cap, s);
-    if (prec == 16 && gf == GF_F16_12) return d32_direct_fmt<RB, MINB, MODE, __half, GF_F16_12>(dag, epi, a, cap, s);
+    if (prec == 16 && gf == GF_F32_12) return d32_direct_fmt<RB, MINB, MODE, __half, GF_F32_12>(dag, epi, a, cap, s);
     return cudaErrorInvalidValue;
 }
 

@@ -562,6 +562,7 @@ struct Solve {
         read_scalars();
         for (int q = 0; q < k; q++) {
             sth[q].iters = 0;
+            sth[q].nit = 0;
             if (!(sth[q].aux > sth[q].target)) sth[q].active = 0;
             if (!std::isfinite(sth[q].aux)) {
                 sth[q].active = 0;
@@ -1289,7 +1290,11 @@ eig_status eig_op_create(const double *gauge, const int dims[4], double m_q, con
     op->m_q = m_q;
     op->prec = o.spinor_prec == 64 ? P64 : (o.spinor_prec == 32 ? P32 : P16);
     op->wprec = op->prec == P64 ? P64 : P32;
-    op->gf_inner = op->prec == P64 ? GF_F64_18 : (op->prec == P32 ? (o.link_compress12 ? GF_F32_12 : GF_F32_18) : GF_F16_12);
+    // half-precision spinors keep FP32 links (12 reals): links rounded to FP16 perturb the
+    // operator the Krylov recurrences see by ~3e-4, and between residual replacements CG
+    // then converges on that operator instead of A (many more iterations at cond 1e4-1e5);
+    // at k RHS per launch the links are 1/k of the stencil's bytes
+    op->gf_inner = op->prec == P64 ? GF_F64_18 : (op->prec == P32 ? (o.link_compress12 ? GF_F32_12 : GF_F32_18) : GF_F32_12);
     op->max_rhs = o.max_rhs;
     op->delta = (o.reliable_delta > 0.0 && o.reliable_delta < 1.0) ? o.reliable_delta : 0.1;
     const int K = o.max_rhs;
@@ -1791,18 +1796,16 @@ eig_status eig_initcg_solve(eig_op op, eig_basis basis, const double *b, double 
     int restarts = 0;
     bool ok = true;
     int rounds = 0;
-    // per-RHS iterations of phase 1 and the global iteration index phase 2 starts from:
-    // a RHS's count is its own phase-1 count plus the phase-2 iterations it took part in
-    // (the batch runs on after a RHS has reached restart_tol, and graph replays issue
-    // iterations past convergence)
-    int j1 = 0;
+    // per-RHS iteration counts (CGScalars::nit) count only the iterations a RHS took part
+    // in: a batch runs on after one RHS has stopped (at restart_tol, at tol, or before a
+    // re-activation by the final residual check)
     std::vector<int> it1(k, 0);
     if (defl && restart_tol > tol) {
         // phase 1: CG to restart_tol, then re-deflate from the current x (Sec. 5.3)
         sv.start(restart_tol);
         ok = cg_run(sv, max_iter, nullptr, op);
-        j1 = sv.j;
-        for (int q = 0; q < k; q++) it1[q] = sv.sth[q].iters;
+        const int j1 = sv.j;
+        for (int q = 0; q < k; q++) it1[q] = sv.sth[q].nit;
         std::vector<int> rel1 = sv.reliable;
         if (ok) {
             sv.true_residual(false, false);  // x64 += x_lo; r64 = b - A x64
@@ -1812,7 +1815,10 @@ eig_status eig_initcg_solve(eig_op op, eig_basis basis, const double *b, double 
             sv.j = j1;
             sv.j_checked = j1;
             for (int q = 0; q < k; q++) sv.reliable[q] += rel1[q];
-            for (int q = 0; q < k; q++) sv.sth[q].iters = j1;
+            for (int q = 0; q < k; q++) {
+                sv.sth[q].iters = j1;
+                sv.sth[q].nit = it1[q];  // each RHS's count goes on from its phase-1 iterations
+            }
             sv.write_scalars();
         }
     } else {
@@ -1830,7 +1836,7 @@ eig_status eig_initcg_solve(eig_op op, eig_basis basis, const double *b, double 
     if (stats) {
         for (int q = 0; q < k; q++) {
             eig_stats &st = stats[q];
-            st.iters = restarts ? it1[q] + (sv.sth[q].iters - j1) : sv.sth[q].iters;
+            st.iters = sv.sth[q].nit;
             st.restarts = restarts;
             st.reliable_updates = sv.reliable[q];
             const double bn2 = sv.sth[q].target / (tol * tol);

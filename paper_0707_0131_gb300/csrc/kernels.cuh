@@ -31,6 +31,7 @@ struct CGScalars {
     int iters;        // last iteration in which this RHS was active
     int x_pending;    // 1: x still lacks alpha * p of the last iteration (applied by the next p update)
     int breakdown;    // 1 if pAp <= 0, NaN or Inf was met
+    int nit;          // iterations this RHS took part in (a batch runs on after a RHS stops)
 };
 
 // Device scalars of one BiCGSTAB solve (complex values as re, im).

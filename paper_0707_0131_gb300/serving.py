@@ -62,7 +62,7 @@ class OpSpec:
         wide = 192 if self.prec == 64 else 96
         # FP64 links, their double-float copy (mixed precision) and the inner formats
         # (FP32 ops keep both the 12- and the 18-real form)
-        links = V * 4 * (144 + (0 if self.prec == 64 else 144) + {64: 0, 32: 48 + 72, 16: 24}[self.prec])
+        links = V * 4 * (144 + (0 if self.prec == 64 else 144) + {64: 0, 32: 48 + 72, 16: 48}[self.prec])
         work = V * self.max_rhs * (3 * sp + 5 * 192 + 2 * wide + 2 * 192) + V * 96 * 4
         window = V * wide * (self.m + 3)
         basis = V * wide * (self.basis_max + self.nev + 16 + 16)

@@ -83,8 +83,8 @@ def test_burst_forms_batches_same_as_alone(serving):
     first init-CG batch is on the GPU is admitted into the next batch (at least one
     batch of more than one RHS forms).  Each batched result equals the same request
     solved alone through the same deflated path (same operator, same basis, k = 1):
-    same iteration count within one, and solutions within 10 tol cond(A), the forward
-    error that two solutions to tol can differ by."""
+    iteration counts within 10%, and solutions within 10 tol cond(A), the forward error
+    that two solutions to tol can differ by."""
     specs = _specs(serving)
     spec = specs[1]  # 8^4, cond(A) ~ 1e3
     srv = serving.Server([spec])
@@ -110,7 +110,8 @@ def test_burst_forms_batches_same_as_alone(serving):
     for b, r in zip(bs, res):
         x = np.zeros_like(b)
         st = w.op.initcg_solve(b, x, tol=spec.tol, restart_tol=spec.restart_tol, basis=w.basis, k=1)[0]
-        assert abs(st["iters"] - r["stats"]["iters"]) <= 1, (st["iters"], r["stats"]["iters"], r["batch"])
+        it_a, it_b = st["iters"], r["stats"]["iters"]
+        assert abs(it_a - it_b) <= max(1, 0.1 * it_a), (it_a, it_b, r["batch"])
         assert np.linalg.norm(r["x"] - x) / np.linalg.norm(x) <= 10 * spec.tol * cond
         assert _check(spec, b, r["x"], spec.tol)
     srv.close()
