@@ -389,8 +389,12 @@ __global__ void k_pupdate(FieldView r, FieldView p, FieldView x, int first, cons
         const long s = g / r.k;
         const int q = (int)(g - s * r.k);
         Spinor<C> rr, pp;
-        SpinorStore<S>::load(r, s, q, rr);
         const CGScalars &sc = st[q];
+        // a RHS that has stopped while others in its batch go on keeps its p (and r, x)
+        // untouched, so that if the final residual check resumes it, it continues exactly as
+        // it would have alone
+        if (!first && !sc.active && !sc.x_pending) continue;
+        SpinorStore<S>::load(r, s, q, rr);
         if (first) {
             pp = rr;
         } else {
@@ -408,7 +412,8 @@ __global__ void k_pupdate(FieldView r, FieldView p, FieldView x, int first, cons
                     }
                 SpinorStore<SV>::store(x, s, q, xx);
             }
-            const C be = sc.active ? (C)sc.beta : (C)0;
+            if (!sc.active) continue;  // x done; p stays
+            const C be = (C)sc.beta;
 #pragma unroll
             for (int i = 0; i < 4; i++)
 #pragma unroll

@@ -481,6 +481,7 @@ struct Solve {
     std::vector<double> rmax;   // max ||r|| since last reliable update
     int j = 0;                  // last issued iteration
     int j_checked = 0;          // history read up to here
+    int j_start = 0;            // iteration index the current CG run (re)started from
     double tol;
     // spectral preconditioner from the first spl vectors of spB (Sec. 2): z = P^{-1} r
     bool sp = false;
@@ -572,6 +573,7 @@ struct Solve {
         write_scalars();
         j = 0;
         j_checked = 0;
+        j_start = 0;
         rmax.assign(k, 0.0);
         for (int q = 0; q < k; q++) rmax[q] = std::sqrt(sth[q].aux);
         reliable.assign(k, 0);
@@ -579,7 +581,10 @@ struct Solve {
 
     // Reliable-update test on the history since the last check (host has read it).
     bool needs_reliable() {
-        if (!mixed) return false;
+        // only iterations since the last check count: right after a (re)start no history of
+        // this run exists yet, and a replacement there would set beta != 0 for a direction
+        // that must be the residual itself
+        if (!mixed || j <= j_checked) return false;
         bool trig = false;
         const double *r_ = hr();
         for (int q = 0; q < k; q++) {
@@ -599,8 +604,8 @@ struct Solve {
     // that near convergence no iterations are launched for RHS that have stopped.
     // Needs the history read up to j.
     int iterations_to_next_check() const {
-        if (j < 2) return CHECK;
-        const int j0 = std::max(1, j - CHECK);
+        if (j - j_start < 2) return CHECK;
+        const int j0 = std::max(j_start + 1, j - CHECK);
         const double *r_ = hr();
         double worst = 0.0;
         for (int q = 0; q < k; q++) {
@@ -720,6 +725,12 @@ static void sp_apply(Solve &sv, int iter) {
     CUDA_CK(launch_pcg_rho(sv.r, sv.z, sv.st, sv.h, iter, sv.red, s));
 }
 
+// EIG_CG_TRACE=1: one line per host check on stderr (diagnostics)
+static bool cg_trace() {
+    const char *e = getenv("EIG_CG_TRACE");
+    return e && e[0] == '1';
+}
+
 // Runs CG iterations until every RHS is inactive or max_iter.  With a window,
 // performs the eigCG additions.  Returns false if max_iter was hit.
 static bool cg_run(Solve &sv, int max_iter, Window *w, eig_op_s *op) {
@@ -746,13 +757,21 @@ static bool cg_run(Solve &sv, int max_iter, Window *w, eig_op_s *op) {
             if (!any) break;
             if (sv.j >= max_iter) return false;
             sv.read_history(sv.j);
-            if (sv.needs_reliable()) {
+            const bool rel = sv.needs_reliable();
+            if (rel) {
                 sv.reliable_update();
                 check_breakdown(sv);
             }
             sv.j_checked = sv.j;
             since = 0;
             next_check = sv.iterations_to_next_check();
+            if (cg_trace()) {
+                fprintf(stderr, "cg j=%d next=%d reliable=%d", sv.j, next_check, (int)rel);
+                for (int q = 0; q < k; q++)
+                    fprintf(stderr, " | q%d act=%d nit=%d rho=%.3e xp=%d", q, sv.sth[q].active, sv.sth[q].nit,
+                            sv.sth[q].rho, sv.sth[q].x_pending);
+                fprintf(stderr, "\n");
+            }
         }
         if (!w && !sv.sp && since == 0 && next_check == CHECK && sv.j >= 1 && sv.j + CHECK <= max_iter &&
             cg_graphs_enabled()) {
@@ -1814,6 +1833,7 @@ eig_status eig_initcg_solve(eig_op op, eig_basis basis, const double *b, double 
             sv.start(tol);
             sv.j = j1;
             sv.j_checked = j1;
+            sv.j_start = j1;
             for (int q = 0; q < k; q++) sv.reliable[q] += rel1[q];
             for (int q = 0; q < k; q++) {
                 sv.sth[q].iters = j1;
