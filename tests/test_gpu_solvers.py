@@ -269,11 +269,11 @@ def test_eigcg_fp32_free_field_ritz_bounds(api):
     Bauer-Fike bound |theta - lambda| <= rho against the closed-form levels, and pairs
     whose residual makes rho^2 / gap small obey the Kato-Temple bound rho^2 / gap.
 
-    In FP32 storage the Ritz pairs of eigCG stall near rho ~ 1e-3 ||A|| / 30: every
-    residual replacement (an FP64 true residual stored back in FP32) breaks the
-    Lanczos relation T = V^H A V at the size of the recursive residual's drift, so no
-    pair reaches the residual (~6e-5 for the lowest level here) that would bound its
-    error below 1e-6 theta.  The 1e-6 bar for converged eigenvalues is tested in FP64
+    In FP32 storage the Ritz pairs of eigCG stall near rho ~ 2e-3 (||A|| ~ 66): the
+    window holds FP32 Lanczos vectors built by FP32 recurrences, and (measured on this
+    problem) the floor does not move when residual replacements are made 1000x rarer.
+    So no pair reaches the residual (~6e-5 for the lowest level here) that would bound
+    its error below 1e-6 theta.  The 1e-6 bar for converged eigenvalues is tested in FP64
     (Incremental eigCG and free-field tests above); here the GPU's values must be as
     accurate as their own residuals say."""
     import itertools
