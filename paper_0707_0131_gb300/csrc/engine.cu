@@ -194,6 +194,7 @@ struct eig_op_s {
     std::vector<CgGraph> graphs;
     DevBuf tcerr;      // error flag of the tensor-core window restart
     PinBuf errh;
+    DevBuf tcb;        // B-operand scratch of the tensor-core A Y (window restart, preconditioner)
     // spectrally preconditioned eigCG: z = P^{-1} r, G = shift H_p^{-1} - I, U_p^H r, G U_p^H r,
     // tensor-core partial sums and error flags
     FieldBuf zsp;
@@ -279,6 +280,7 @@ struct eig_basis_s {
     bool chol_ok = true;
     DevBuf C, Y;            // device small matrices
     DevBuf tcpart, tcerr;   // partial sums and error flag of the tensor-core U^H R
+    DevBuf tcb;             // B-operand scratch of the tensor-core A Y
     PinBuf Ch, errh;
     long gen = 0;           // bumped whenever U changes
     // BiCGSTAB deflation through g5 M: Z = lowest Ritz vectors of A in span(U) and
@@ -718,10 +720,12 @@ static void sp_apply(Solve &sv, int iter) {
     CUDA_CK(launch_sp_coef(op->spG.as<double>(), op->spC.as<double>(), op->spY.as<double>(), sv.spl, s));
     CUDA_CK(launch_combine(sv.z, 1.0, sv.r, 0.0, null_field(), s));
     const ColSet Z = field_cols(sv.z.v.data, f64, 1, nrow, 1, true);
-    if (tc_gemm_enabled() && (nrow % 2) == 0 && tc_ay_ok(U, Z))
-        CUDA_CK(launch_tc_ay(U, op->spY.as<double>(), Z, 1.0, nrow, op->sperr.as<int>() + 1, s));
-    else
+    if (tc_gemm_enabled() && (nrow % 2) == 0 && tc_ay_ok(U, Z)) {
+        op->tcb.ensure(TC_AY_SCRATCH);
+        CUDA_CK(launch_tc_ay(U, op->spY.as<double>(), Z, 1.0, nrow, op->sperr.as<int>() + 1, op->tcb.p, s));
+    } else {
         CUDA_CK(launch_gemm_ay(U, op->spY.as<double>(), Z, 1.0, nrow, s));
+    }
     CUDA_CK(launch_pcg_rho(sv.r, sv.z, sv.st, sv.h, iter, sv.red, s));
 }
 
@@ -857,7 +861,9 @@ static bool cg_run(Solve &sv, int max_iter, Window *w, eig_op_s *op) {
                     op->tcerr.ensure(16);
                     op->errh.ensure(16);
                     CUDA_CK(cudaMemsetAsync(op->tcerr.p, 0, 16, s));
-                    CUDA_CK(launch_tc_ay(Vw, op->qz.as<double>(), Out, 0.0, op->ncomplex(), op->tcerr.as<int>(), s));
+                    op->tcb.ensure(TC_AY_SCRATCH);
+                    CUDA_CK(launch_tc_ay(Vw, op->qz.as<double>(), Out, 0.0, op->ncomplex(), op->tcerr.as<int>(),
+                                         op->tcb.p, s));
                     CUDA_CK(launch_wdot(tc, tp, sv.h.beta + (size_t)j * k, op->win.p, op->col_off.as<long>(), nout,
                                         op->ncomplex(), op->wv.as<double>(), sv.red, s));
                     CUDA_CK(cudaMemcpyAsync(op->errh.p, op->tcerr.p, 4, cudaMemcpyDeviceToHost, s));
@@ -1064,7 +1070,8 @@ static void ay_run(eig_basis_s *B, const ColSet &A, const double *Y, const ColSe
         B->tcerr.ensure(16);
         B->errh.ensure(16);
         CUDA_CK(cudaMemsetAsync(B->tcerr.p, 0, 16, s));
-        CUDA_CK(launch_tc_ay(A, Y, Out, beta, nrow, B->tcerr.as<int>(), s));
+        B->tcb.ensure(TC_AY_SCRATCH);
+        CUDA_CK(launch_tc_ay(A, Y, Out, beta, nrow, B->tcerr.as<int>(), B->tcb.p, s));
         CUDA_CK(cudaMemcpyAsync(B->errh.p, B->tcerr.p, 4, cudaMemcpyDeviceToHost, s));
         sync(s);
         if (*B->errh.as<int>() != 0) throw Error{EIG_ERR_TIMEOUT, "tensor-core A Y: a bounded wait in the kernel gave up"};

@@ -218,8 +218,12 @@ cudaError_t launch_tc_ahb(const ColSet &A, const ColSet &B, long nrows, double *
 // nA x nOut row-major on the device; nrows even.  *err (device, zeroed by the caller)
 // becomes non-zero if a bounded wait gave up (Out is then invalid).
 bool tc_ay_ok(const ColSet &A, const ColSet &Out);
+// bscratch: device scratch of at least TC_AY_SCRATCH bytes owned by the caller's handle
+// (the B operand of every K chunk, built once per launch); calls that overlap on the GPU
+// must use different scratch
+constexpr size_t TC_AY_SCRATCH = 32 * 2 * 8192;  // up to 512 columns of A, N = 64
 cudaError_t launch_tc_ay(const ColSet &A, const double *Y, const ColSet &Out, double beta, long nrows, int *err,
-                         cudaStream_t s);
+                         void *bscratch, cudaStream_t s);
 
 // Copies the sites of one parity between a full-lattice FP64 field and a half-lattice
 // FP64 field (to_half: full -> half), same k; Lx even.

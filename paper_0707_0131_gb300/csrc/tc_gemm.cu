@@ -454,7 +454,33 @@ struct AyArgs {
     long nrows;
     int mtiles, nch;   // M tiles, K chunks
     int *err;
+    // B operand of every K chunk, split into TF32 hi and lo and laid out as the MMA reads
+    // it (K-major, 128-byte swizzle): [chunk][hi, lo][N / 8 KB], built once per launch
+    const unsigned char *Bpre;
 };
+
+// Builds AyArgs::Bpre from Y: row r = 2c + e of chunk kc's B tile holds, at K position
+// 2 al + e' (basis column kc * AY_COLS + al, its re / im part e'), the real coefficient that
+// turns (re, im) of U[n, col] into part e of output column c of the complex product U y
+template <int N>
+__global__ void k_ay_prep_b(const double *Y, int nA, int k, int nch, unsigned char *Bpre) {
+    constexpr uint32_t b_bytes = (uint32_t)(N / 8) * 1024;
+    const long total = (long)nch * N * KT;
+    for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+        const int kc = (int)(idx / (N * KT)), rem = (int)(idx % (N * KT));
+        const int r = rem / KT, kk = rem % KT, al = kk >> 1, ep = kk & 1, c = r >> 1, e = r & 1;
+        const int col = kc * AY_COLS + al;
+        float y = 0.f;
+        if (c < k && col < nA) {
+            const double yr = Y[2 * ((long)col * k + c)], yi = Y[2 * ((long)col * k + c) + 1];
+            y = (float)(e == 0 ? (ep == 0 ? yr : -yi) : (ep == 0 ? yi : yr));
+        }
+        const float yh = hi_tf32(y);
+        unsigned char *base = Bpre + (size_t)kc * 2 * b_bytes;
+        *reinterpret_cast<float *>(base + sw128(r, kk)) = yh;
+        *reinterpret_cast<float *>(base + b_bytes + sw128(r, kk)) = y - yh;
+    }
+}
 
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
     asm volatile(
@@ -580,17 +606,6 @@ __global__ void __launch_bounds__(AY_THREADS, 1) k_tc_ay(const AyArgs a) {
     } else {
         // ---------------- workers ----------------
         const int wt = t - 64, quarter = warp & 3, half = (warp - 2) >> 2;
-        constexpr int NB = N * KT / (32 * WORKERS);  // Yt elements per worker thread
-        auto load_y = [&](int j, double2 *yv) {
-#pragma unroll
-            for (int m = 0; m < NB; m++) {
-                const int i = wt + m * 32 * WORKERS, r = i / KT, al = (i % KT) >> 1, c = r >> 1;
-                const int col = (j % a.nch) * AY_COLS + al;
-                yv[m] = make_double2(0.0, 0.0);
-                if (j < njobs && c < a.k && col < a.nA)
-                    yv[m] = reinterpret_cast<const double2 *>(a.Y)[(long)col * a.k + c];
-            }
-        };
         // outputs of tile ti (rows n0 ..), from accumulator ti & 1; warp-uniform
         auto epilogue = [&](int ti) {
             const bool ok = __all_sync(0xffffffffu, mbar_wait(&acc_full[ti & 1], (ti >> 1) & 1));
@@ -645,8 +660,6 @@ __global__ void __launch_bounds__(AY_THREADS, 1) k_tc_ay(const AyArgs a) {
             }
             return true;
         };
-        double2 ycur[NB], ynext[NB];
-        load_y(0, ycur);
         int j = 0, pending = -1;  // tile whose outputs are still to be written
         bool ok = true;
         for (; j < njobs && ok && !abort_flag; j++) {
@@ -654,7 +667,6 @@ __global__ void __launch_bounds__(AY_THREADS, 1) k_tc_ay(const AyArgs a) {
             const long n0 = (long)job_tile(j) * TM;
             const long rows = min((long)TM, a.nrows - n0);
             const int nc = min(AY_COLS, a.nA - kc * AY_COLS);
-            load_y(j + 1, ynext);
             if (!__all_sync(0xffffffffu, mbar_wait(&stg_full[s], (j / AY_NSTG) & 1))) {
                 fail(15);
                 break;
@@ -693,18 +705,13 @@ __global__ void __launch_bounds__(AY_THREADS, 1) k_tc_ay(const AyArgs a) {
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&stg_free[s]);  // the staging slot has been read
-            // B = Yt for this chunk: row r = 2c + e (output c, re/im), K position 2 al + e'
-#pragma unroll
-            for (int m = 0; m < NB; m++) {
-                const int i = wt + m * 32 * WORKERS, r = i / KT, kk = i % KT, ep = kk & 1, e = r & 1;
-                const double yr = ycur[m].x, yi = ycur[m].y;
-                const float y = (float)(e == 0 ? (ep == 0 ? yr : -yi) : (ep == 0 ? yi : yr));
-                const float yh = hi_tf32(y);
-                *reinterpret_cast<float *>(Bhi + sw128(r, kk)) = yh;
-                *reinterpret_cast<float *>(Blo + sw128(r, kk)) = y - yh;
+            // B = Yt for this chunk: a copy of the tiles k_ay_prep_b built (hi, then lo; the two
+            // are contiguous in the operand buffer as in Bpre)
+            {
+                const float4 *src = reinterpret_cast<const float4 *>(a.Bpre + (size_t)kc * 2 * b_bytes);
+                float4 *dst = reinterpret_cast<float4 *>(Bhi);
+                for (int i = wt; i < (int)(2 * b_bytes / 16); i += 32 * WORKERS) dst[i] = __ldg(src + i);
             }
-#pragma unroll
-            for (int m = 0; m < NB; m++) ycur[m] = ynext[m];
             asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
             __syncwarp();
             if (lane == 0) mbar_arrive(&op_ready[o]);
@@ -843,8 +850,8 @@ bool tc_ay_ok(const ColSet &A, const ColSet &Out) {
 // Out = beta Out + A Y (FP32 column sets, Y FP64 nA x nOut complex row-major, device).
 // A's column offsets (col_off) must be even, as every window slot offset is.
 cudaError_t launch_tc_ay(const ColSet &A, const double *Y, const ColSet &Out, double beta, long nrows, int *err,
-                         cudaStream_t s) {
-    if (!tc_ay_ok(A, Out) || (nrows & 1)) return cudaErrorInvalidValue;
+                         void *bscratch, cudaStream_t s) {
+    if (!tc_ay_ok(A, Out) || (nrows & 1) || !bscratch) return cudaErrorInvalidValue;
     ProfScope prof("tc_gemm_ay", (double)nrows * (A.ncols + Out.ncols * (beta != 0.0 ? 2 : 1)) * 8.0, s);
     AyArgs a;
     a.A = static_cast<const float2 *>(A.base);
@@ -862,7 +869,17 @@ cudaError_t launch_tc_ay(const ColSet &A, const double *Y, const ColSet &Out, do
     a.mtiles = (int)((nrows + TM - 1) / TM);
     a.nch = (A.ncols + AY_COLS - 1) / AY_COLS;
     a.err = err;
+    a.Bpre = static_cast<const unsigned char *>(bscratch);
     const int N = 2 * Out.ncols <= 16 ? 16 : (2 * Out.ncols <= 32 ? 32 : 64);
+    if ((size_t)a.nch * 2 * (size_t)(N / 8) * 1024 > TC_AY_SCRATCH) return cudaErrorInvalidValue;
+    {
+        unsigned char *bp = static_cast<unsigned char *>(bscratch);
+        const int nprep = a.nch * N * KT;
+        const int pg = (nprep + 255) / 256;
+        if (N == 16) k_ay_prep_b<16><<<pg, 256, 0, s>>>(Y, a.nA, a.k, a.nch, bp);
+        else if (N == 32) k_ay_prep_b<32><<<pg, 256, 0, s>>>(Y, a.nA, a.k, a.nch, bp);
+        else k_ay_prep_b<64><<<pg, 256, 0, s>>>(Y, a.nA, a.k, a.nch, bp);
+    }
     int grid = device_sm_count();
     if (grid > a.mtiles) grid = a.mtiles;
     const int nstg = N <= 32 ? 6 : 5;  // AyStages<N>
