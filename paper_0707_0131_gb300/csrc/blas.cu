@@ -376,7 +376,7 @@ cudaError_t launch_norm2(Field f, CGScalars *st, bool as_rho, History h, int ite
 // ---------------------------------------------------------------------------------------
 template <typename S, typename SV>
 __global__ void k_pupdate(FieldView r, FieldView p, FieldView x, int first, const CGScalars *st, FieldView v,
-                          int append) {
+                          int append, unsigned long long *dev_bytes) {
     using C = typename SpinorStore<S>::C;
     using CV = typename SpinorStore<SV>::C;
     {
@@ -384,21 +384,25 @@ __global__ void k_pupdate(FieldView r, FieldView p, FieldView x, int first, cons
         for (int q = 0; q < r.k; q++) any = any || st[q].active;
         if (!any) return;
     }
+    constexpr unsigned SB = SpinorStore<S>::BYTES, SBV = SpinorStore<SV>::BYTES;
+    unsigned moved = 0;  // bytes this thread read and wrote
     const long total = r.V * r.k;
     for (long g = (long)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += (long)gridDim.x * blockDim.x) {
         const long s = g / r.k;
         const int q = (int)(g - s * r.k);
-        Spinor<C> rr, pp;
         const CGScalars &sc = st[q];
         // a RHS that has stopped while others in its batch go on keeps its p (and r, x)
         // untouched, so that if the final residual check resumes it, it continues exactly as
         // it would have alone
         if (!first && !sc.active && !sc.x_pending) continue;
-        SpinorStore<S>::load(r, s, q, rr);
+        Spinor<C> rr, pp;
         if (first) {
+            SpinorStore<S>::load(r, s, q, rr);
             pp = rr;
+            moved += SB;
         } else {
             SpinorStore<S>::load(p, s, q, pp);
+            moved += SB;
             if (sc.x_pending) {  // Fig. 1 step 13 of the previous iteration
                 const CV al = (CV)sc.alpha;
                 Spinor<CV> xx;
@@ -411,8 +415,11 @@ __global__ void k_pupdate(FieldView r, FieldView p, FieldView x, int first, cons
                         xx.s[i][j].im += al * (CV)pp.s[i][j].im;
                     }
                 SpinorStore<SV>::store(x, s, q, xx);
+                moved += 2 * SBV;
             }
             if (!sc.active) continue;  // x done; p stays
+            SpinorStore<S>::load(r, s, q, rr);
+            moved += SB;
             const C be = (C)sc.beta;
 #pragma unroll
             for (int i = 0; i < 4; i++)
@@ -421,6 +428,7 @@ __global__ void k_pupdate(FieldView r, FieldView p, FieldView x, int first, cons
                     pp.s[i][j] = cmk<C>(rr.s[i][j].re + be * pp.s[i][j].re, rr.s[i][j].im + be * pp.s[i][j].im);
         }
         SpinorStore<S>::store(p, s, q, pp);
+        moved += SB;
         if (append && sc.active) {
             const CV sc_inv = (CV)(1.0 / sqrt(sc.rho));
             Spinor<CV> vv;
@@ -429,7 +437,12 @@ __global__ void k_pupdate(FieldView r, FieldView p, FieldView x, int first, cons
 #pragma unroll
                 for (int j = 0; j < 3; j++) vv.s[i][j] = cmk<CV>((CV)rr.s[i][j].re * sc_inv, (CV)rr.s[i][j].im * sc_inv);
             SpinorStore<SV>::store(v, s, q, vv);
+            moved += SBV;
         }
+    }
+    if (dev_bytes) {
+        const unsigned w = __reduce_add_sync(0xffffffffu, moved);
+        if ((threadIdx.x & 31) == 0 && w) atomicAdd(dev_bytes, (unsigned long long)w);
     }
 }
 
@@ -437,23 +450,29 @@ cudaError_t launch_pupdate(Field r, Field p, Field x, bool first, CGScalars *st,
     const int app = v_append.v.data != nullptr;
     // per batch width, like the stencils: k = 1 fields (85 MB at 24^3x64) partly stay in L2
     const std::string pname = r.v.k > 1 ? "pupdate_k" + std::to_string(r.v.k) : std::string("pupdate");
-    ProfScope prof(pname.c_str(), (double)r.v.V * r.v.k * ((first ? 2.0 : 3.0) * spb(r.prec) + (first ? 0.0 : 2.0 * spb(x.prec))) +
-                                      (app ? (double)r.v.V * spb(v_append.prec) : 0.0), s);
+    // bytes: counted by the kernel while timing is on (RHS that have stopped move nothing),
+    // else the estimate for every RHS active
+    unsigned long long *devb = prof_device_bytes(pname.c_str());
+    ProfScope prof(pname.c_str(),
+                   devb ? 0.0
+                        : (double)r.v.V * r.v.k * ((first ? 2.0 : 3.0) * spb(r.prec) + (first ? 0.0 : 2.0 * spb(x.prec))) +
+                              (app ? (double)r.v.V * spb(v_append.prec) : 0.0),
+                   s);
     const int B = 128;
     const int G = stream_grid(r.v.V * r.v.k, B);
     if (app && v_append.prec != x.prec) return cudaErrorInvalidValue;
     switch (r.prec) {
         case P64:
             if (x.prec != P64) return cudaErrorInvalidValue;
-            k_pupdate<double, double><<<G, B, 0, s>>>(r.v, p.v, x.v, first, st, v_append.v, app);
+            k_pupdate<double, double><<<G, B, 0, s>>>(r.v, p.v, x.v, first, st, v_append.v, app, devb);
             break;
         case P32:
             if (x.prec != P32) return cudaErrorInvalidValue;
-            k_pupdate<float, float><<<G, B, 0, s>>>(r.v, p.v, x.v, first, st, v_append.v, app);
+            k_pupdate<float, float><<<G, B, 0, s>>>(r.v, p.v, x.v, first, st, v_append.v, app, devb);
             break;
         case P16:
             if (x.prec != P32) return cudaErrorInvalidValue;
-            k_pupdate<__half, float><<<G, B, 0, s>>>(r.v, p.v, x.v, first, st, v_append.v, app);
+            k_pupdate<__half, float><<<G, B, 0, s>>>(r.v, p.v, x.v, first, st, v_append.v, app, devb);
             break;
     }
     return cudaGetLastError();

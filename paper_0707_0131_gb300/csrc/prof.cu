@@ -20,6 +20,10 @@ std::vector<Entry> g_entries;
 std::vector<cudaEvent_t> g_pool;
 bool g_timing = false;
 thread_local ProfRecord *g_rec = nullptr;
+// bytes counted on the device by kernels whose traffic depends on device state (one
+// counter per entry slot); allocated when timing is first enabled
+constexpr int MAX_DEV = 64;
+unsigned long long *g_dev = nullptr;
 
 int slot_of(const char *name) {
     for (size_t i = 0; i < g_entries.size(); i++)
@@ -85,10 +89,26 @@ bool prof_timing() {
 void prof_enable(bool on) {
     std::lock_guard<std::mutex> lk(g_mu);
     g_timing = on;
+    if (on && !g_dev) {
+        if (cudaMalloc(&g_dev, MAX_DEV * sizeof(unsigned long long)) != cudaSuccess) {
+            g_dev = nullptr;
+            cudaGetLastError();
+        } else {
+            cudaMemset(g_dev, 0, MAX_DEV * sizeof(unsigned long long));
+        }
+    }
+}
+
+unsigned long long *prof_device_bytes(const char *name) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_timing || !g_dev || g_rec) return nullptr;
+    const int sl = slot_of(name);
+    return sl < MAX_DEV ? g_dev + sl : nullptr;
 }
 
 void prof_reset() {
     cudaDeviceSynchronize();
+    if (g_dev) cudaMemset(g_dev, 0, MAX_DEV * sizeof(unsigned long long));
     std::lock_guard<std::mutex> lk(g_mu);
     for (auto &e : g_entries) {
         for (auto &pr : e.pending) {
@@ -104,9 +124,16 @@ void prof_reset() {
 
 int prof_read(KernelStat *out, int max) {
     cudaDeviceSynchronize();
+    unsigned long long dev[MAX_DEV] = {0};
+    if (g_dev) {
+        cudaMemcpy(dev, g_dev, sizeof(dev), cudaMemcpyDeviceToHost);
+        cudaMemset(g_dev, 0, sizeof(dev));
+    }
     std::lock_guard<std::mutex> lk(g_mu);
     int n = 0;
-    for (auto &e : g_entries) {
+    for (size_t i = 0; i < g_entries.size(); i++) {
+        auto &e = g_entries[i];
+        if (i < (size_t)MAX_DEV) e.bytes += (double)dev[i];
         for (auto &pr : e.pending) {
             float ms = 0.f;
             if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess) e.ms += ms;

@@ -38,6 +38,11 @@ void prof_replay(const ProfRecord &rec);
 bool prof_timing();
 
 void prof_enable(bool on);
+// While timing is on (and not while capturing a graph): a device counter, in bytes, for the
+// entry `name`, which kernels whose traffic depends on device state (RHS that have stopped
+// move nothing) add to; prof_read folds it into the entry's bytes.  nullptr otherwise: the
+// caller then charges its host-side estimate.
+unsigned long long *prof_device_bytes(const char *name);
 void prof_reset();
 // Synchronises the device, folds pending event pairs into the totals.
 int prof_read(KernelStat *out, int max);
