@@ -59,8 +59,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="skip the short serving phase of the solve benchmark")
+    ap.add_argument("--no-eo", action="store_true", help="skip the odd-even arm of the solve benchmark")
     ap.add_argument("--serve-requests", type=int, default=48, help="solve mode: requests of the serving phase")
-    ap.add_argument("--mode", default="solve", choices=["solve", "dslash", "serve", "bicgstab"],
+    ap.add_argument("--mode", default="solve", choices=["solve", "dslash", "serve", "bicgstab", "oracle"],
                     help="dslash: only repeated matvecs through eig_op_apply (kernel GB/s); "
                          "serve: Poisson requests over 9 operators through the serving loop")
     ap.add_argument("--requests", type=int, default=200, help="serve mode: number of requests")
@@ -208,6 +209,32 @@ def run_reference(a):
                                       f"{iters_per_rhs} iterations per RHS, configs/bench.json)"},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
+
+
+def run_oracle(a):
+    """Timings of the FP64 CPU oracle on this machine's host cores (a reported baseline, not
+    the target): full CG and eigCG solves at 4^4, 8^4 and 16^3x32 and a full CG solve at
+    24^3x64, all at cond(A) ~ 1e3 and tol 1e-8, plus seconds per CG iteration at 24^3x64."""
+    import oracle
+    from oracle import solvers
+
+    rows = []
+    for name in ("4^4", "8^4", "16^3x32", "24^3x64"):
+        dims = fx.LATTICES[name]
+        m_q, src = mass_for(name, "1e+03")
+        W = oracle.Wilson(dims, m_q, fx.make_gauge(dims, fx.GAUGE_SEEDS[name]))
+        b = fx.make_rhs(dims, fx.rhs_seed(name, 0))[0].reshape(-1)
+        for kind in ("cg", "eigcg"):
+            if kind == "eigcg" and name == "24^3x64":
+                continue
+            t0 = time.perf_counter()
+            o = solvers.cg(W, b, tol=1e-8) if kind == "cg" else solvers.eigcg(W, b, nev=10, m=100, tol=1e-8)
+            dt = time.perf_counter() - t0
+            rows.append({"lattice": name, "solver": kind, "iters": int(o["iters"]), "seconds": dt,
+                         "s_per_iter": dt / max(1, o["iters"]), "true_rel_res": float(o["true_rel_res"]),
+                         "mass": src})
+            print(json.dumps(rows[-1]), flush=True)
+    print(json.dumps({"mode": "oracle", "cores": oracle.num_threads(), "solves": rows}), flush=True)
 
 
 def run_dslash(a):
@@ -388,6 +415,9 @@ def main():
     if a.mode == "dslash":
         run_dslash(a)
         return
+    if a.mode == "oracle":
+        run_oracle(a)
+        return
     if a.mode == "bicgstab":
         run_bicgstab(a)
         return
@@ -511,7 +541,7 @@ def main():
     if os.path.exists(tfile):
         h = hashlib.sha1()
         for f in ("dslash32.cuh", "dslash32.cu", "dslash32d_rb1.cu", "dslash32d_rb2.cu", "dslash32pp.cuh",
-                  "dslash32p2.cu", "dslash32p3.cu"):
+                  "dslash32p2.cu", "dslash32p3.cu", "dslash32p3f.cu"):
             h.update(open(os.path.join(ROOT, "paper_0707_0131_gb300", "csrc", f), "rb").read())
         for tj in json.load(open(tfile)).get(kern, []):
             if (tj.get("stencil_sha1") == h.hexdigest() and tj.get("variant") == kvar
@@ -577,6 +607,36 @@ def main():
         x10 = torch.zeros_like(B1[0])
         dt, sts = timed(lambda: op.initcg_solve(b1, x10, a.tol, a.restart_tol, basis=basis, k=1))
         arms["deflated_initcg_fp32_k1"] = {"value": 1 / dt, "unit": UNIT, "iters_mean": float(sts[0]["iters"])}
+
+    # --- the odd-even form (Sec. 5's operator): M x = b through the odd-site Schur complement,
+    # Incremental eigCG to the same basis size on A_hat = M_hat^H M_hat, then a k-RHS init-CG
+    if not a.no_plain and not a.no_eo:
+        op_eo = Op(gauge, dims, m_q, prec=a.prec, max_rhs=k, compress12=a.links == 12,
+                   reliable_delta=a.reliable_delta, even_odd=True)
+        basis_eo = Basis(op_eo, a.basis + a.nev)
+        t0 = time.perf_counter()
+        grow_iters = []
+        while basis_eo.size + a.nev <= a.basis:
+            b = torch.from_numpy(next_rhs(1)[0]).to(dev)
+            st = op_eo.eigcg_solve(b, torch.zeros_like(b), a.nev, a.m, a.tol, basis=basis_eo)
+            basis_eo.grow()
+            grow_iters.append(st["iters"])
+        setup_eo = time.perf_counter() - t0
+        bk = torch.from_numpy(next_rhs(k)).to(dev)
+        xk0 = torch.zeros_like(bk)
+        dt, sts = timed(lambda: op_eo.initcg_solve(bk, xk0, a.tol, a.restart_tol, basis=basis_eo, k=k))
+        arms[f"eo_deflated_initcg_fp32_k{k}"] = {
+            "value": k / dt, "unit": UNIT, "iters_mean": float(np.mean([q["iters"] for q in sts])),
+            "max_true_rel_res": float(max(q["true_rel_res"] for q in sts)), "basis": basis_eo.size,
+            "setup_s": setup_eo, "eigcg_iters_first_last": [grow_iters[0], grow_iters[-1]] if grow_iters else None,
+            "system": "M x = b on the full lattice, solved through the odd-site Schur complement "
+                      "(CG on M_hat^H M_hat, residual of those normal equations <= tol)"}
+        xk0 = torch.zeros_like(bk)
+        dt, sts = timed(lambda: op_eo.initcg_solve(bk, xk0, a.tol, k=k, max_iter=20000))
+        arms[f"eo_plain_cg_fp32_k{k}"] = {"value": k / dt, "unit": UNIT,
+                                          "iters_mean": float(np.mean([q["iters"] for q in sts]))}
+        basis_eo.close()
+        op_eo.close()
 
     # --- serving: Poisson single-RHS requests on this operator and basis --------------
     serve = None

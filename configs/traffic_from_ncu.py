@@ -20,7 +20,7 @@ import os
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 STENCIL_SOURCES = ["dslash32.cuh", "dslash32.cu", "dslash32d_rb1.cu", "dslash32d_rb2.cu", "dslash32pp.cuh",
-                   "dslash32p2.cu", "dslash32p3.cu"]
+                   "dslash32p2.cu", "dslash32p3.cu", "dslash32p3f.cu"]
 
 
 def stencil_sha1() -> str:

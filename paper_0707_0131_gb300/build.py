@@ -19,7 +19,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libeigcg.so")
-SOURCES = ["dslash.cu", "dslash32.cu", "dslash32d_rb1.cu", "dslash32d_rb2.cu", "dslash32p2.cu", "dslash32p3.cu", "dslash_dd.cu", "blas.cu", "gemm.cu", "tc_gemm.cu", "engine.cu", "prof.cu", "noalloc.cu", "bicgstab.cu", "dense.cpp"]
+SOURCES = ["dslash.cu", "dslash32.cu", "dslash32d_rb1.cu", "dslash32d_rb2.cu", "dslash32p2.cu", "dslash32p3.cu", "dslash32p3f.cu", "dslash_dd.cu", "blas.cu", "gemm.cu", "tc_gemm.cu", "engine.cu", "prof.cu", "noalloc.cu", "bicgstab.cu", "dense.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -27,12 +27,13 @@ std::unordered_map<const void *, int> g_occ32;
 //  16  pipelined pair (dslash32pp.cuh): 2 adjacent RHS per thread, 256-bit loads, the
 //      next hop's loads in flight while the current one is computed, 2 blocks/SM
 //  17  as 16, 3 blocks/SM        18, 19: 16, 17 over the tiled site traversal
+//  20  as 17, plus an L1 prefetch of the hop after next;  21: 20 over the tiled site traversal
 // The fastest valid one is chosen per (volume, k, storage, link format) by
-// autotune_dslash32 and cached; EIG_DSLASH_VARIANT=0..19 in the environment forces one.
-constexpr int NVAR = 20;
+// autotune_dslash32 and cached; EIG_DSLASH_VARIANT=0..21 in the environment forces one.
+constexpr int NVAR = 22;
 
 bool is_pp(int v) { return v >= 16; }
-bool is_tiled(int v) { return (v >= 8 && v < 16) || v >= 18; }
+bool is_tiled(int v) { return (v >= 8 && v < 16) || v == 18 || v == 19 || v == 21; }
 
 int variant_rb(int v) {
     if (is_pp(v)) return 2;
@@ -164,6 +165,7 @@ cudaError_t launch_rb(const K32 &a, int cap, cudaStream_t s) {
     if (is_tiled(v)) tile_setup(b, variant_rb(v));
     if (is_pp(v)) {
         if (!pp_aligned(b)) return d32_launch_direct_rb2(4, prec, GF, DAG, EPI, b, cap, s);
+        if (v == 20 || v == 21) return d32_launch_pp3f(prec, GF, DAG, EPI, b, cap, s);
         return (v == 16 || v == 18) ? d32_launch_pp2(prec, GF, DAG, EPI, b, cap, s)
                                     : d32_launch_pp3(prec, GF, DAG, EPI, b, cap, s);
     }

@@ -75,6 +75,8 @@ cudaError_t d32_launch_direct_rb2(int variant, int prec, int gf, bool dag, int e
 // per SM; k >= 2, fields 32-byte aligned)
 cudaError_t d32_launch_pp2(int prec, int gf, bool dag, int epi, const K32 &a, int cap, cudaStream_t s);
 cudaError_t d32_launch_pp3(int prec, int gf, bool dag, int epi, const K32 &a, int cap, cudaStream_t s);
+// as d32_launch_pp3, with an L1 prefetch of the hop after next (dslash32p3f.cu)
+cudaError_t d32_launch_pp3f(int prec, int gf, bool dag, int epi, const K32 &a, int cap, cudaStream_t s);
 // grid for a launch of `kern` (TPB threads, `smem` bytes of dynamic shared memory):
 // resident blocks per SM x SMs, no more blocks than `work` threads need, at most cap
 int d32_grid(const void *kern, long work, int cap, size_t smem);

@@ -179,7 +179,24 @@ __device__ __forceinline__ void hop_pair(const PairRaw<S> &d, const LinkRaw<GF> 
     }
 }
 
-template <typename S, int GF, bool DAG, int EPI, int MINB>
+// PF: also ask L1 for the spinor pair and link of hop h + 2 while hop h is computed (no
+// registers held for it), so that the register load of hop h + 1 finds them closer
+template <typename S, int GF>
+__device__ __forceinline__ void prefetch_pair(const K32 &a, unsigned o, int mu, unsigned ls) {
+#pragma unroll
+    for (int c = 0; c < PairRaw<S>::NC; c++) pf_l1(a.in + c * a.P + o);
+    if (GF == GF_F32_12) {
+        const float4 *g = static_cast<const float4 *>(a.g) + (unsigned)mu * 3u * a.Vg;
+#pragma unroll
+        for (int i = 0; i < 3; i++) pf_l1(g + i * a.Vg + ls);
+    } else {
+        const float2 *g = static_cast<const float2 *>(a.g) + (unsigned)mu * 9u * a.Vg;
+#pragma unroll
+        for (int e = 0; e < 9; e += 2) pf_l1(g + e * a.Vg + ls);
+    }
+}
+
+template <typename S, int GF, bool DAG, int EPI, int MINB, bool PF = false>
 __global__ void __launch_bounds__(TPB, MINB) k_dslash32pp(const K32 a) {
     __shared__ double smem[(TPB / 32) * MAX_RHS];
     if (EPI != E_PLAIN) {
@@ -254,6 +271,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_dslash32pp(const K32 a) {
 #pragma unroll
         for (int h = 0; h < 8; h++) {
             const int cur = h & 1, nx = cur ^ 1;
+            if (PF && h + 2 < 8) prefetch_pair<S, GF>(a, nbr[h + 2] * a.k + r0, (h + 2) >> 1, lks[h + 2]);
             if (h < 7) {
                 load_pair<S, true>(a.in, a.in_s, a.P, nbr[h + 1] * a.k + r0, sp[nx]);
                 lk[nx].load(a.g, a.Vg, (h + 1) >> 1, lks[h + 1]);
@@ -360,20 +378,22 @@ __global__ void __launch_bounds__(TPB, MINB) k_dslash32pp(const K32 a) {
     });
 }
 
-template <int MINB, typename S, int GF, bool DAG, int EPI>
+template <int MINB, bool PF, typename S, int GF, bool DAG, int EPI>
 cudaError_t d32pp_go(const K32 &a, int cap, cudaStream_t s) {
-    auto kern = k_dslash32pp<S, GF, DAG, EPI, MINB>;
+    auto kern = k_dslash32pp<S, GF, DAG, EPI, MINB, PF>;
     kern<<<d32_grid((const void *)kern, (long)a.V * a.k / 2, cap, 0), TPB, 0, s>>>(a);
     return cudaGetLastError();
 }
 
-template <int MINB, typename S, int GF>
+template <int MINB, bool PF, typename S, int GF>
 cudaError_t d32pp_fmt(bool dag, int epi, const K32 &a, int cap, cudaStream_t s) {
     if (epi == E_PLAIN)
-        return dag ? d32pp_go<MINB, S, GF, true, E_PLAIN>(a, cap, s) : d32pp_go<MINB, S, GF, false, E_PLAIN>(a, cap, s);
+        return dag ? d32pp_go<MINB, PF, S, GF, true, E_PLAIN>(a, cap, s)
+                   : d32pp_go<MINB, PF, S, GF, false, E_PLAIN>(a, cap, s);
     if (epi == E_NORM)
-        return dag ? d32pp_go<MINB, S, GF, true, E_NORM>(a, cap, s) : d32pp_go<MINB, S, GF, false, E_NORM>(a, cap, s);
-    return dag ? d32pp_go<MINB, S, GF, true, E_CG>(a, cap, s) : d32pp_go<MINB, S, GF, false, E_CG>(a, cap, s);
+        return dag ? d32pp_go<MINB, PF, S, GF, true, E_NORM>(a, cap, s)
+                   : d32pp_go<MINB, PF, S, GF, false, E_NORM>(a, cap, s);
+    return dag ? d32pp_go<MINB, PF, S, GF, true, E_CG>(a, cap, s) : d32pp_go<MINB, PF, S, GF, false, E_CG>(a, cap, s);
 }
 
 }  // namespace

@@ -3,7 +3,7 @@
 The library picks the fastest of the stencil variants (staged or direct loads, one or two
 RHS per thread, register budgets, L1 prefetch, lexicographic or tiled site traversal:
 variants 8 + v, tiled on 8^4 and untiled on the ragged lattice; the pipelined-pair
-variants 16-19 with 256-bit loads, k >= 2 only) per lattice and k;
+variants 16-21 with 256-bit loads, k >= 2 only) per lattice and k;
 EIG_DSLASH_VARIANT forces one
 for the whole process (EIG_DSLASH_LINKS the FP32 link format: 12 or 18 reals), so
 each variant runs in a subprocess of its own.  Each one
@@ -61,7 +61,7 @@ print("variant ok")
 
 @pytest.mark.parametrize("variant,links", [(v, None) for v in range(8)] + [(v, "18") for v in (2, 4, 6)]
                          + [(v, None) for v in (10, 12, 14, 15)] + [(14, "18")]
-                         + [(v, None) for v in (16, 17, 18, 19)] + [(16, "18"), (18, "18")])
+                         + [(v, None) for v in (16, 17, 18, 19, 20, 21)] + [(16, "18"), (18, "18"), (21, "18")])
 def test_variant_parity(variant, links):
     import torch
 
@@ -96,7 +96,7 @@ def test_stencil_choice_reported():
     X = np.zeros_like(B)
     op.initcg_solve(B, X, tol=1e-6, k=2)
     v, g = op.stencil_choice(2)
-    assert 0 <= v <= 19 and g in (12, 18), (v, g)
+    assert 0 <= v <= 21 and g in (12, 18), (v, g)
     v1, g1 = op.stencil_choice(1)
     assert (v1, g1) == (-1, 0)  # k = 1 not solved yet
     with pytest.raises(Exception):
