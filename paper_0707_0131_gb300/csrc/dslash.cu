@@ -491,18 +491,6 @@ cudaError_t launch_dslash_norm(const DslashCall &c, CGScalars *st, History h, in
     return dispatch<EPI_NORM>(c, a, red.max_blocks, s);
 }
 
-cudaError_t launch_dslash_normp(const DslashCall &c, Field p, Field x, bool first, CGScalars *st, History h,
-                                int iter, RedScratch red, cudaStream_t s) {
-    if (c.in.prec == P64) return cudaErrorInvalidValue;
-    const double sp = c.in.prec == P32 ? 96 : 52;
-    // r gathered, u read and written, p read and written, x (FP32) read and written
-    const double bytes = (double)c.V * site_bytes_gauge(c.gformat) + (double)c.V * c.k * (5 * sp + 2 * 96.0);
-    std::string name = std::string(c.in.prec == P32 ? "dslash_normp_f32" : "dslash_normp_f16");
-    if (c.k > 1) name += "_k" + std::to_string(c.k);
-    ProfScope prof(name.c_str(), bytes, s);
-    return launch_dslash32_normp(c, p, x, first, st, h, iter, red, s);
-}
-
 cudaError_t launch_dslash_cg(const DslashCall &c, Field r, Field t_save, CGScalars *st, History h, int iter,
                              RedScratch red, cudaStream_t s) {
     KArgs a = base_args(c);

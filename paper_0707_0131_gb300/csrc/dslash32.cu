@@ -52,10 +52,8 @@ bool variant_ok(int v, unsigned k, int gf) {
 // must start on a 32-byte boundary (scale arrays on an 8-byte one); they do not write the
 // single-RHS t_prev copy of eigCG
 bool pp_aligned(const K32 &a) {
-    const uintptr_t f = (uintptr_t)a.in | (uintptr_t)a.out | (uintptr_t)a.r | (uintptr_t)a.cen | (uintptr_t)a.pf |
-                        (uintptr_t)a.x;
-    const uintptr_t sc = (uintptr_t)a.in_s | (uintptr_t)a.out_s | (uintptr_t)a.r_s | (uintptr_t)a.cen_s |
-                         (uintptr_t)a.pf_s;
+    const uintptr_t f = (uintptr_t)a.in | (uintptr_t)a.out | (uintptr_t)a.r | (uintptr_t)a.cen;
+    const uintptr_t sc = (uintptr_t)a.in_s | (uintptr_t)a.out_s | (uintptr_t)a.r_s | (uintptr_t)a.cen_s;
     return (f & 31) == 0 && (sc & 7) == 0 && !a.save_t;
 }
 
@@ -161,16 +159,7 @@ cudaError_t launch_rb(const K32 &a, int cap, cudaStream_t s) {
     // (extents >= 2)
     if (a.k == 0 || (a.k & (a.k - 1)) != 0 || a.L0 < 2 || a.L1 < 2 || a.L2 < 2) return cudaErrorInvalidValue;
     const int prec = sizeof(S) == 4 ? 32 : 16;
-    int v = variant_for(a, prec, GF);
-    if constexpr (EPI == E_NORMP) {  // only the pipelined-pair variants carry the fused p update
-        if (a.k < 2 || a.eo >= 0 || !pp_aligned(a)) return cudaErrorInvalidValue;
-        if (!is_pp(v)) v = 17;
-        K32 b = a;
-        if (is_tiled(v)) tile_setup(b, 2);
-        if (v == 20 || v == 21) return d32_launch_pp3f(prec, GF, DAG, EPI, b, cap, s);
-        return (v == 16 || v == 18) ? d32_launch_pp2(prec, GF, DAG, EPI, b, cap, s)
-                                    : d32_launch_pp3(prec, GF, DAG, EPI, b, cap, s);
-    }
+    const int v = variant_for(a, prec, GF);
     if (v <= 1) return launch_staged<S, GF, DAG, EPI>(variant_rb(v), a, cap, s);
     K32 b = a;
     if (is_tiled(v)) tile_setup(b, variant_rb(v));
@@ -375,25 +364,6 @@ cudaError_t launch_dslash32_norm(const DslashCall &c, CGScalars *st, History h, 
     a.partials = red.partials;
     a.counter = red.counter;
     return dispatch32<E_NORM>(c, a, red.max_blocks, s);
-}
-
-cudaError_t launch_dslash32_normp(const DslashCall &c, Field p, Field x, bool first, CGScalars *st, History h,
-                                  int iter, RedScratch red, cudaStream_t s) {
-    if (c.dagger || x.prec != P32) return cudaErrorInvalidValue;
-    K32 a = args32(c);
-    a.pf = static_cast<float4 *>(p.v.data);
-    a.pf_s = p.v.scale;
-    a.x = static_cast<float4 *>(x.v.data);
-    a.first = first ? 1 : 0;
-    a.st = st;
-    a.h_alpha = h.alpha;
-    a.h_beta = h.beta;
-    a.h_rho = h.rho;
-    a.iter = iter;
-    a.jbase = h.jbase;
-    a.partials = red.partials;
-    a.counter = red.counter;
-    return dispatch32<E_NORMP>(c, a, red.max_blocks, s);
 }
 
 cudaError_t launch_dslash32_cg(const DslashCall &c, Field r, Field t_save, CGScalars *st, History h, int iter,

@@ -36,9 +36,6 @@ struct K32 {
     float *r_s;
     float4 *x;     // FP32 x (always FP32 storage)
     float4 *tsave; // FP32, k = 1
-    float4 *pf;    // E_NORMP: the search direction p (read and written), its scales
-    float *pf_s;
-    int first;     // E_NORMP: first iteration (p = r, u = M r)
     const void *g;
     unsigned L0, L1, L2, L3, V;  // V: output sites (V / 2 in the odd-even form)
     unsigned Vg;                 // lattice sites: stride of the link planes
@@ -511,9 +508,7 @@ __device__ __forceinline__ void prefetch_hop(const K32 &a, unsigned ns, unsigned
     }
 }
 
-// E_NORMP (pipelined-pair variants only): CG pass 1 with the p update of the same
-// iteration fused in (dslash32pp.cuh)
-enum { E_PLAIN = 0, E_NORM = 1, E_CG = 2, E_NORMP = 3 };
+enum { E_PLAIN = 0, E_NORM = 1, E_CG = 2 };
 
 // MODE 0: loads staged through the cp.async ring (Pipe); MODE 1: loads straight to
 // registers, with MINB blocks per SM requested from the register allocator; MODE 2:

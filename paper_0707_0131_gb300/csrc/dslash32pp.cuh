@@ -312,63 +312,6 @@ __global__ void __launch_bounds__(TPB, MINB) k_dslash32pp(const K32 a) {
                 nrm[0] += norm2f(out[0]);
                 nrm[1] += norm2f(out[1]);
             }
-        } else if (EPI == E_NORMP) {
-            // CG pass 1 with the p update fused in: in = r, so out = M r and the centre term is
-            // r.  p_new = r + beta p_old (Fig. 1 step 9) and, by linearity,
-            // u_new = M p_new = M r + beta u_old; x += alpha p_old (step 13 of the previous
-            // iteration, where pending).  A RHS that has stopped keeps p and u.
-            PairRaw<S> praw;
-            load_pair<S, false>(a.pf, a.pf_s, a.P, o, praw);
-            Sp pold[2];
-            unpack_pair<S>(praw, 0, pold[0]);
-            unpack_pair<S>(praw, 1, pold[1]);
-            const CGScalars &s0 = a.st[r0], &s1 = a.st[r0 + 1];
-            if (!a.first && (s0.x_pending || s1.x_pending)) {
-                PairRaw<float> xr;
-                load_pair<float, false>(a.x, nullptr, a.P, o, xr);
-                Sp xx[2];
-#pragma unroll
-                for (int q = 0; q < 2; q++) {
-                    unpack_pair<float>(xr, q, xx[q]);
-                    const CGScalars &st = q ? s1 : s0;
-                    const float al = st.x_pending ? (float)st.alpha : 0.f;
-#pragma unroll
-                    for (int e = 0; e < 12; e++) xx[q].c[e] = fma2(f2(al, al), pold[q].c[e], xx[q].c[e]);
-                }
-                store_pair<float>(a.x, nullptr, a.P, o, xx);
-            }
-            PairRaw<S> uraw;
-            if (!a.first) load_pair<S, false>(a.out, a.out_s, a.P, o, uraw);
-            Sp pn[2], un[2];
-#pragma unroll
-            for (int q = 0; q < 2; q++) {
-                const CGScalars &st = q ? s1 : s0;
-                Sp rc;  // r at the centre
-                if (have_cen) unpack_pair<S>(sp[0], q, rc);
-                else
-#pragma unroll
-                    for (int e = 0; e < 12; e++) rc.c[e] = f2(0.f, 0.f);
-                if (a.first) {
-                    pn[q] = rc;
-                    un[q] = out[q];
-                } else {
-                    unpack_pair<S>(uraw, q, un[q]);
-                    if (st.active) {
-                        const float be = (float)st.beta;
-                        const F2 b2 = f2(be, be);
-#pragma unroll
-                        for (int e = 0; e < 12; e++) {
-                            pn[q].c[e] = fma2(b2, pold[q].c[e], rc.c[e]);
-                            un[q].c[e] = fma2(b2, un[q].c[e], out[q].c[e]);
-                        }
-                    } else {
-                        pn[q] = pold[q];
-                    }
-                }
-                if (st.active) nrm[q] += norm2f(un[q]);
-            }
-            store_pair<S>(a.pf, a.pf_s, a.P, o, pn);
-            store_pair<S>(a.out, a.out_s, a.P, o, un);
         } else {  // E_CG: r -= alpha t
             Sp rr[2];
 #pragma unroll
@@ -399,7 +342,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_dslash32pp(const K32 a) {
     grid_finish_rhs(k, a.partials, a.counter, smem, [=](int r, double tot) {
         CGScalars &st = sts[r];
         const long hi = (long)iter * k + r;
-        if (EPI == E_NORM || EPI == E_NORMP) {
+        if (EPI == E_NORM) {
             if (st.active) {
                 st.pAp = tot;
                 if (!(tot > 0.0) || !isfinite(tot)) {
@@ -444,7 +387,6 @@ cudaError_t d32pp_go(const K32 &a, int cap, cudaStream_t s) {
 
 template <int MINB, bool PF, typename S, int GF>
 cudaError_t d32pp_fmt(bool dag, int epi, const K32 &a, int cap, cudaStream_t s) {
-    if (epi == E_NORMP) return d32pp_go<MINB, PF, S, GF, false, E_NORMP>(a, cap, s);  // M only
     if (epi == E_PLAIN)
         return dag ? d32pp_go<MINB, PF, S, GF, true, E_PLAIN>(a, cap, s)
                    : d32pp_go<MINB, PF, S, GF, false, E_PLAIN>(a, cap, s);

@@ -646,24 +646,12 @@ static bool cg_graphs_enabled() {
     return !(e && e[0] == '0');
 }
 
-// CG pass 1 with the p update fused in (FP32 / FP16 storage, k >= 2, full lattice;
-// EIG_CG_FUSE=0 turns it off): u = M p is formed as M r + beta u, so that the p update's
-// streaming traffic runs inside the latency-bound stencil instead of as a kernel of its own.
-// The first iteration after every host check uses the separate p update and M p, so u is
-// recomputed from p at least every CHECK iterations.
-static bool cg_fuse_enabled(const Solve &sv) {
-    const char *e = getenv("EIG_CG_FUSE");
-    if (e && e[0] == '0') return false;
-    return sv.mixed && sv.k >= 2 && !sv.op->eo;
-}
-
 // The graph of CHECK iterations j0 + 1 .. j0 + CHECK for this solve's buffers (j0 is
 // read by the kernels from op->jbase_dev), captured on first use.
 static cudaGraphExec_t cg_graph(Solve &sv, eig_op_s *op) {
-    const bool fuse = cg_fuse_enabled(sv);
     const std::vector<const void *> key = {(const void *)(long)sv.k, sv.r.v.data, sv.p.v.data, sv.u.v.data,
                                            sv.xlo.v.data, sv.st, sv.h.alpha, sv.h.beta, sv.h.rho,
-                                           (const void *)(long)op->prec, (const void *)(long)fuse};
+                                           (const void *)(long)op->prec};
     for (auto &g : op->graphs)
         if (g.key == key) return g.exec;
     op->jbase_dev.ensure(16);
@@ -681,13 +669,9 @@ static cudaGraphExec_t cg_graph(Solve &sv, eig_op_s *op) {
     prof_record_begin(&gr.rec);
     cudaError_t e = cudaSuccess;
     for (int t = 1; t <= CHECK && e == cudaSuccess; t++) {
-        if (fuse && t > 1) {
-            e = launch_dslash_normp(op->call(sv.r, sv.u, false, false), sv.p, sv.xlo, false, sv.st, hg, t, sv.red, s);
-        } else {
-            e = launch_pupdate(sv.r, sv.p, sv.xlo, false, sv.st, null_field(), s);
-            if (e == cudaSuccess)
-                e = launch_dslash_norm(mcall(op, sv.p, sv.u, false, op->prec == P64, s), sv.st, hg, t, sv.red, s);
-        }
+        e = launch_pupdate(sv.r, sv.p, sv.xlo, false, sv.st, null_field(), s);
+        if (e == cudaSuccess)
+            e = launch_dslash_norm(mcall(op, sv.p, sv.u, false, op->prec == P64, s), sv.st, hg, t, sv.red, s);
         if (e == cudaSuccess)
             e = launch_dslash_cg(mcall(op, sv.u, sv.u, true, op->prec == P64, s), sv.r, null_field(), sv.st, hg, t,
                                  sv.red, s);
@@ -831,13 +815,8 @@ static bool cg_run(Solve &sv, int max_iter, Window *w, eig_op_s *op) {
             vapp = field_at(op->wprec, (char *)op->win.p + (size_t)slot * op->wfield_bytes(), op->Vf, 1);
         }
         if (sv.sp) sp_apply(sv, j - 1);  // Fig. 1 steps 3-4 and 8 with P != I
-        if (!w && !sv.sp && since > 1 && cg_fuse_enabled(sv)) {
-            CUDA_CK(launch_dslash_normp(op->call(sv.r, sv.u, false, false), sv.p, sv.xlo, j == 1, sv.st, sv.h, j,
-                                        sv.red, s));
-        } else {
-            CUDA_CK(launch_pupdate(sv.sp ? sv.z : sv.r, sv.p, sv.xlo, j == 1, sv.st, vapp, s));
-            CUDA_CK(launch_dslash_norm(mcall(op, sv.p, sv.u, false, op->prec == P64, s), sv.st, sv.h, j, sv.red, s));
-        }
+        CUDA_CK(launch_pupdate(sv.sp ? sv.z : sv.r, sv.p, sv.xlo, j == 1, sv.st, vapp, s));
+        CUDA_CK(launch_dslash_norm(mcall(op, sv.p, sv.u, false, op->prec == P64, s), sv.st, sv.h, j, sv.red, s));
         Field tsave = null_field();
         if (w) {
             const bool becomes_full = !restart_now && (w->i + 1 == w->m);

@@ -113,13 +113,6 @@ cudaError_t launch_dslash32_norm(const DslashCall &c, CGScalars *st, History h, 
                                  cudaStream_t s);
 cudaError_t launch_dslash32_cg(const DslashCall &c, Field r, Field t_save, CGScalars *st, History h, int iter,
                                RedScratch red, cudaStream_t s);
-// CG pass 1 with the p update fused in (k >= 2, FP32 / FP16 storage, full lattice):
-// c.in = r, c.out = u; p = r + beta p (p = r when first), u = M p computed as
-// M r + beta u (u = M r when first), x += alpha p_old where pending, then as pass 1.
-cudaError_t launch_dslash32_normp(const DslashCall &c, Field p, Field x, bool first, CGScalars *st, History h,
-                                  int iter, RedScratch red, cudaStream_t s);
-cudaError_t launch_dslash_normp(const DslashCall &c, Field p, Field x, bool first, CGScalars *st, History h,
-                                int iter, RedScratch red, cudaStream_t s);
 // chooses (once per volume, k and format) how many RHS each stencil thread handles
 // Times every stencil variant on c's buffers (in -> out), for c's link format and for
 // the same links stored in each of the n_alts other formats gf_alts (data gauge_alts);
