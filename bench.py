@@ -396,6 +396,7 @@ def run_serve(a):
            "batched_fraction": float(np.mean([r["batch"] > 1 for _, r in res])),
            "batch_histogram": srv.batch_histogram(),
            "max_hbm_used_gb": srv.max_used / 1e9, "budget_gb": a.budget_gb,
+           "workspaces_released": srv.trims, "operators_closed": srv.closes,
            "eigcg_solves": int(sum(r["kind"] == "eigcg" for _, r in res)),
            "config": {"workload": f"{len(specs)} operators ({a.serve_lattices} x cond 1e3/1e4/1e5), basis "
                                   f"<= {a.serve_basis}, eigCG({a.nev},{a.m}) then init-CG batches of <= {a.k}, tol {a.tol}",

@@ -39,6 +39,8 @@
 #ifndef EIGCG_H
 #define EIGCG_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -98,6 +100,14 @@ typedef struct {
 eig_status eig_op_create(const double *gauge, const int dims[4], double m_q, const eig_op_opts *opts,
                          eig_op *out);
 eig_status eig_op_destroy(eig_op op);
+/* Releases the op's workspace (Krylov fields for max_rhs RHS, FP64 and natural-layout
+ * staging, the eigCG window, the captured CG graphs) and keeps the links; bases bound to
+ * the op keep their vectors and H.  The next call that needs the workspace allocates it
+ * again.  For a serving loop that holds more operators' bases than it can give
+ * workspaces at once (no counterpart in the paper).  Synchronises the device.  *freed
+ * (may be NULL): bytes released.  Errors: EIG_ERR_ARG, EIG_ERR_CUDA; a later call may
+ * return EIG_ERR_OOM when the workspace no longer fits. */
+eig_status eig_op_trim(eig_op op, size_t *freed);
 
 /* out = M in (which 0), M^H in (which 1) or A in (which 2) for k RHS (1..max_rhs),
  * in the op's storage precision; which 3 (FP32/FP16 ops only) applies A in the

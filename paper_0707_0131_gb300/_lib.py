@@ -82,6 +82,7 @@ SIGNATURES = {
     "eig_profile_enable": [_I],
     "eig_profile_reset": [],
     "eig_profile_read": [_P, _I, _P],
+    "eig_op_trim": [_P, _P],
     "eig_profile_alu_peak": [_I, _P, _P],
     "eig_wilson_apply_noalloc": [_P, _P, _D, _I, _P, _P, _P],
     "eig_last_error": [],
@@ -282,6 +283,13 @@ def eig_basis_load(basis, path, stream=None) -> None:
 
 def eig_profile_enable(on: bool = True) -> None:
     _check(load().eig_profile_enable(1 if on else 0))
+
+
+def eig_op_trim(op) -> int:
+    """Releases the op's workspace (bases keep their vectors); returns the bytes freed."""
+    v = ctypes.c_size_t(0)
+    _check(load().eig_op_trim(op, ctypes.byref(v)))
+    return int(v.value)
 
 
 def eig_profile_alu_peak(prec: int, stream=None) -> float:

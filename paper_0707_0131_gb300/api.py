@@ -39,6 +39,10 @@ class Op:
         except Exception:
             pass
 
+    def trim(self):
+        """Releases the workspace (allocated again by the next call); bases keep their vectors."""
+        return _lib.eig_op_trim(self.h)
+
     def apply(self, which, vin, vout, k=1, stream=None):
         _lib.eig_op_apply(self.h, which, vin, vout, k, stream)
         return vout

@@ -119,6 +119,11 @@ struct FieldBuf {
         data.alloc(field_bytes(p, v, k));
         if (p == P16) scale.alloc((size_t)v * k * sizeof(float));
     }
+    void release() {
+        data.release();
+        scale.release();
+        kcap = 0;
+    }
     Field view(int k) const {
         Field f;
         f.prec = prec;
@@ -207,6 +212,7 @@ struct eig_op_s {
     DevBuf jbase_dev;  // iteration base the replayed kernels add to their offsets
     PinBuf jbase_h;
     cudaStream_t cap_stream = nullptr;  // private stream the graphs are captured on
+    bool ws = false;                    // workspace allocated (see ensure_workspace)
     ~eig_op_s() {
         for (auto &g : graphs)
             if (g.exec) cudaGraphExecDestroy(g.exec);
@@ -296,6 +302,53 @@ struct eig_basis_s {
 namespace eig {
 
 static void set_error(const Error &e) { g_last_error = e.msg; }
+
+// The workspace of an op: the Krylov fields for max_rhs RHS, FP64 staging and the
+// natural-layout staging (fields of Vf sites: half-lattice fields for the odd-even form).
+// Allocated when the op is created; eig_op_trim releases it together with the eigCG window
+// and the CUDA graphs that point into it, and the next call that needs it allocates it again.
+static void ensure_workspace(eig_op_s *op) {
+    if (op->ws) return;
+    const long Vf = op->Vf, V = op->V;
+    const int K = op->max_rhs;
+    op->r.alloc(op->prec, Vf, K);
+    op->p.alloc(op->prec, Vf, K);
+    op->u.alloc(op->prec, Vf, K);
+    op->b64.alloc(P64, Vf, K);
+    op->x64.alloc(P64, Vf, K);
+    op->u64.alloc(P64, Vf, K);
+    if (op->prec != P64) {
+        op->xlo.alloc(P32, Vf, K);
+        op->r64.alloc(P64, Vf, K);
+    }
+    op->rsv.alloc(op->wprec, Vf, K);
+    op->xsv.alloc(op->wprec, Vf, K);
+    if (op->eo) {
+        op->tmp_e.alloc(op->prec, Vf, K);
+        op->tmp64_e.alloc(P64, Vf, K);
+        op->full64.alloc(P64, V, K);
+        op->be64.alloc(P64, Vf, K);
+    }
+    op->nat_in.alloc((size_t)V * 12 * 16 * K);
+    op->nat_out.alloc((size_t)V * 12 * 16 * K);
+    op->ws = true;
+}
+
+static void release_workspace(eig_op_s *op) {
+    for (auto &g : op->graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    op->graphs.clear();
+    for (FieldBuf *f : {&op->r, &op->p, &op->u, &op->b64, &op->x64, &op->u64, &op->xlo, &op->r64, &op->rsv, &op->xsv,
+                        &op->tmp_e, &op->tmp64_e, &op->full64, &op->be64, &op->zsp, &op->bc_rh, &op->bc_s, &op->bc_t})
+        f->release();
+    op->nat_in.release();
+    op->nat_out.release();
+    op->win.release();
+    op->win_slots = 0;
+    op->tprev.release();
+    op->tcur.release();
+    op->ws = false;
+}
 
 // lets entry points defined in other files report a message through eig_last_error
 void set_last_error_message(const char *msg) { g_last_error = msg ? msg : ""; }
@@ -1346,28 +1399,7 @@ eig_status eig_op_create(const double *gauge, const int dims[4], double m_q, con
         }
     }
     CUDA_CK(cudaDeviceSynchronize());
-    // workspace (fields of Vf sites: half-lattice fields for the odd-even form)
-    const long Vf = op->Vf;
-    op->r.alloc(op->prec, Vf, K);
-    op->p.alloc(op->prec, Vf, K);
-    op->u.alloc(op->prec, Vf, K);
-    op->b64.alloc(P64, Vf, K);
-    op->x64.alloc(P64, Vf, K);
-    op->u64.alloc(P64, Vf, K);
-    if (op->prec != P64) {
-        op->xlo.alloc(P32, Vf, K);
-        op->r64.alloc(P64, Vf, K);
-    }
-    op->rsv.alloc(op->wprec, Vf, K);
-    op->xsv.alloc(op->wprec, Vf, K);
-    if (op->eo) {
-        op->tmp_e.alloc(op->prec, Vf, K);
-        op->tmp64_e.alloc(P64, Vf, K);
-        op->full64.alloc(P64, V, K);
-        op->be64.alloc(P64, Vf, K);
-    }
-    op->nat_in.alloc((size_t)V * 12 * 16 * K);
-    op->nat_out.alloc((size_t)V * 12 * 16 * K);
+    ensure_workspace(op.get());
     op->st.alloc(sizeof(CGScalars) * MAX_RHS);
     op->st_h.ensure(sizeof(CGScalars) * MAX_RHS);
     op->red_partials.alloc((size_t)RED_BLOCKS * MAX_RHS * 64 * sizeof(double));
@@ -1387,6 +1419,22 @@ eig_status eig_op_destroy(eig_op op) {
     API_END
 }
 
+eig_status eig_op_trim(eig_op op, size_t *freed) {
+    API_BEGIN
+    ARG_CHECK(op, "null argument");
+    std::lock_guard<std::mutex> lk(op->mu);
+    CUDA_CK(cudaDeviceSynchronize());
+    size_t bytes = 0;
+    for (const FieldBuf *f : {&op->r, &op->p, &op->u, &op->b64, &op->x64, &op->u64, &op->xlo, &op->r64, &op->rsv,
+                              &op->xsv, &op->tmp_e, &op->tmp64_e, &op->full64, &op->be64, &op->zsp, &op->bc_rh,
+                              &op->bc_s, &op->bc_t})
+        bytes += f->data.n + f->scale.n;
+    bytes += op->nat_in.n + op->nat_out.n + op->win.n + op->tprev.n + op->tcur.n;
+    release_workspace(op);
+    if (freed) *freed = bytes;
+    API_END
+}
+
 eig_status eig_op_apply(eig_op op, int which, const double *in, double *out, int k, void *stream) {
     API_BEGIN
     ARG_CHECK(op && in && out, "null argument");
@@ -1395,6 +1443,7 @@ eig_status eig_op_apply(eig_op op, int which, const double *in, double *out, int
     ARG_CHECK(which != 3 || !op->eo, "which = 3 is not available for odd-even operators");
     ARG_CHECK(k >= 1 && k <= op->max_rhs && (k & (k - 1)) == 0, "k must be a power of two <= max_rhs");
     std::lock_guard<std::mutex> lk(op->mu);
+    ensure_workspace(op);
     cudaStream_t s = (cudaStream_t)stream;
     Field x64 = op->x64.view(k);
     load_natural(op, in, x64, s);
@@ -1510,6 +1559,7 @@ static eig_status eigcg_impl(eig_op op, eig_basis basis, const double *b, double
     ARG_CHECK(max_iter >= 1 && max_iter <= 10000000, "max_iter out of range");
     ARG_CHECK(!basis || basis->op == op, "basis belongs to another op");
     std::lock_guard<std::mutex> lk(op->mu);
+    ensure_workspace(op);
     auto t0 = std::chrono::steady_clock::now();
     cudaStream_t s = (cudaStream_t)stream;
     // window storage: m + 1 slots, t_prev, t_cur
@@ -1663,6 +1713,7 @@ eig_status eig_basis_grow(eig_basis B, void *stream) {
     ARG_CHECK(B, "null argument");
     std::lock_guard<std::mutex> lk(B->mu);
     std::lock_guard<std::mutex> lk2(B->op->mu);
+    ensure_workspace(B->op);
     eig_op_s *op = B->op;
     cudaStream_t s = (cudaStream_t)stream;
     const int np = B->npend;
@@ -1784,6 +1835,7 @@ eig_status eig_basis_deflate(eig_basis B, const double *b, const double *x_in, d
     ARG_CHECK(k >= 1 && k <= op->max_rhs && (k & (k - 1)) == 0, "k must be a power of two <= max_rhs");
     std::lock_guard<std::mutex> lk(B->mu);
     std::lock_guard<std::mutex> lk2(op->mu);
+    ensure_workspace(op);
     cudaStream_t s = (cudaStream_t)stream;
     Field b64 = op->b64.view(k), x64 = op->x64.view(k), r64 = (op->prec == P64 ? op->r : op->r64).view(k);
     load_natural(op, b, b64, s);
@@ -1810,6 +1862,7 @@ eig_status eig_initcg_solve(eig_op op, eig_basis basis, const double *b, double 
     ARG_CHECK(max_iter >= 1 && max_iter <= 10000000, "max_iter out of range");
     ARG_CHECK(!basis || basis->op == op, "basis belongs to another op");
     std::lock_guard<std::mutex> lk(op->mu);
+    ensure_workspace(op);
     auto t0 = std::chrono::steady_clock::now();
     cudaStream_t s = (cudaStream_t)stream;
     Solve sv = make_solve(op, k, s, max_iter);
@@ -1891,6 +1944,7 @@ eig_status eig_bicgstab_solve(eig_op op, eig_basis basis, const double *b, doubl
     ARG_CHECK(defl_vecs >= 0, "defl_vecs must be >= 0");
     ARG_CHECK(!basis || basis->op == op, "basis belongs to another op");
     std::lock_guard<std::mutex> lk(op->mu);
+    ensure_workspace(op);
     auto t0 = std::chrono::steady_clock::now();
     cudaStream_t s = (cudaStream_t)stream;
     if (op->prec != P64) tune_for(op, 1, s);
@@ -1993,6 +2047,7 @@ eig_status eig_basis_ritz(eig_basis B, double *evals, double *resnorms, int *n, 
     ARG_CHECK(B && evals && n, "null argument");
     std::lock_guard<std::mutex> lk(B->mu);
     std::lock_guard<std::mutex> lk2(B->op->mu);
+    ensure_workspace(B->op);
     eig_op_s *op = B->op;
     cudaStream_t s = (cudaStream_t)stream;
     const int l = B->l;
@@ -2038,6 +2093,7 @@ eig_status eig_basis_vector(eig_basis B, int j, double *out, void *stream) {
     ARG_CHECK(B && out, "null argument");
     ARG_CHECK(j >= 0 && j < B->l, "j out of range");
     std::lock_guard<std::mutex> lk(B->op->mu);
+    ensure_workspace(B->op);
     eig_op_s *op = B->op;
     cudaStream_t s = (cudaStream_t)stream;
     Field uc = field_at(op->wprec, (char *)B->U.p + (size_t)j * op->wfield_bytes(), op->Vf, 1);
@@ -2068,6 +2124,7 @@ eig_status eig_basis_save(eig_basis B, const char *path, void *stream) {
     API_BEGIN
     ARG_CHECK(B && path, "null argument");
     std::lock_guard<std::mutex> lk(B->op->mu);
+    ensure_workspace(B->op);
     eig_op_s *op = B->op;
     cudaStream_t s = (cudaStream_t)stream;
     BasisFileHeader h;
@@ -2113,6 +2170,7 @@ eig_status eig_basis_load(eig_basis B, const char *path, void *stream) {
     API_BEGIN
     ARG_CHECK(B && path, "null argument");
     std::lock_guard<std::mutex> lk(B->op->mu);
+    ensure_workspace(B->op);
     eig_op_s *op = B->op;
     cudaStream_t s = (cudaStream_t)stream;
     File in;

@@ -12,9 +12,13 @@ Sec. 5.3) of up to max_rhs right-hand sides.
 Every operator has its own worker thread and CUDA stream, so solves for
 different operators overlap on the GPU; requests that arrive while a batch is
 running are admitted into the next batch of their operator.  Operators are
-admitted under an HBM budget: an operator is activated (its device memory
-allocated) only when its footprint fits next to the active ones; otherwise its
-requests wait until an idle operator has been retired.
+admitted under an HBM budget in two tiers: an operator's resident part (links
+and deflation basis, the state the incremental method builds up) and its
+workspace (Krylov fields, staging, the eigCG window).  An operator is activated
+when its workspace (and, the first time, its resident part) fits next to what is
+held; otherwise idle operators give their workspace back (eig_op_trim, the basis
+stays), and only if that is not enough is the least recently used idle operator
+closed and its basis dropped.
 
 This module only schedules calls; all arithmetic runs in libeigcg.so.
 """
@@ -52,21 +56,32 @@ class OpSpec:
     expected_requests: int = 0
     eigcg_overhead: float = 1.2
     # an operator and basis that already exist (Op, Basis): served as they are, never
-    # closed by the server; its footprint still counts against the budget
+    # trimmed or closed by the server; its footprint still counts against the budget
     prebuilt: tuple = None
 
-    def footprint(self) -> int:
-        """Device bytes of an active operator: links, workspace, window, basis."""
+    def resident_bytes(self) -> int:
+        """Device bytes an operator keeps while idle: links in all forms, the basis."""
+        V = int(np.prod(self.dims))
+        wide = 192 if self.prec == 64 else 96
+        # FP64 links, their double-float copy (mixed precision) and the inner formats
+        # (FP32 ops keep both the 12- and the 18-real form, FP16 ops the 12-real one)
+        links = V * 4 * (144 + (0 if self.prec == 64 else 144) + {64: 0, 32: 48 + 72, 16: 48}[self.prec])
+        basis = V * wide * (self.basis_max + self.nev + 16 + 16)
+        return links + basis
+
+    def workspace_bytes(self) -> int:
+        """Device bytes of an active operator's workspace: Krylov fields for max_rhs RHS,
+        FP64 and natural-layout staging, the eigCG window."""
         V = int(np.prod(self.dims))
         sp = {64: 192, 32: 96, 16: 52}[self.prec]
         wide = 192 if self.prec == 64 else 96
-        # FP64 links, their double-float copy (mixed precision) and the inner formats
-        # (FP32 ops keep both the 12- and the 18-real form)
-        links = V * 4 * (144 + (0 if self.prec == 64 else 144) + {64: 0, 32: 48 + 72, 16: 48}[self.prec])
         work = V * self.max_rhs * (3 * sp + 5 * 192 + 2 * wide + 2 * 192) + V * 96 * 4
         window = V * wide * (self.m + 3)
-        basis = V * wide * (self.basis_max + self.nev + 16 + 16)
-        return links + work + window + basis
+        return work + window
+
+    def footprint(self) -> int:
+        """Device bytes of an active operator."""
+        return self.resident_bytes() + self.workspace_bytes()
 
 
 @dataclass
@@ -93,19 +108,32 @@ class _Worker:
         self.thread = threading.Thread(target=self._run, daemon=True, name=f"eig-{spec.key}")
         self.thread.start()
 
+    @property
+    def resident(self) -> bool:
+        return self.op is not None
+
     def activate(self):
         import torch
 
-        self.stream = torch.cuda.Stream()
+        if self.stream is None:
+            self.stream = torch.cuda.Stream()
         s = self.spec
-        if s.prebuilt is not None:
-            self.op, self.basis = s.prebuilt
-        else:
-            self.op = Op(s.gauge, s.dims, s.m_q, prec=s.prec, max_rhs=s.max_rhs)
-            self.basis = Basis(self.op, s.basis_max + s.nev)
-        self.active = True
+        if self.op is None:
+            if s.prebuilt is not None:
+                self.op, self.basis = s.prebuilt
+            else:
+                self.op = Op(s.gauge, s.dims, s.m_q, prec=s.prec, max_rhs=s.max_rhs)
+                self.basis = Basis(self.op, s.basis_max + s.nev)
+        self.active = True  # a trimmed op allocates its workspace again at its next call
 
-    def retire(self):
+    def trim(self):
+        """Gives the workspace back and keeps the basis."""
+        if self.op is not None and self.spec.prebuilt is None:
+            self.op.trim()
+        self.active = False
+
+    def close(self):
+        """Drops the operator and its basis."""
         if self.spec.prebuilt is None:
             if self.basis is not None:
                 self.basis.close()
@@ -113,6 +141,7 @@ class _Worker:
                 self.op.close()
         self.op = self.basis = None
         self.active = False
+        self.growing = True
 
     def _take(self, first: Request, limit: int):
         batch = [first]
@@ -196,6 +225,8 @@ class Server:
         self.latencies = []
         self.records = []
         self.max_used = 0.0
+        self.trims = 0   # workspaces given back by idle operators
+        self.closes = 0  # idle operators closed (basis dropped)
 
     def submit(self, key: str, b: np.ndarray) -> Future:
         req = Request(key, np.ascontiguousarray(b, dtype=np.complex128).reshape(-1))
@@ -203,21 +234,32 @@ class Server:
         self.workers[key].q.put(req)
         return req.future
 
-    # admission by HBM budget: activate the operator, retiring idle ones if needed
+    # admission by HBM budget: activate the operator; first take workspaces back from idle
+    # operators (their bases stay), then close the least recently used idle operator
     def _admit(self, w: _Worker):
-        need = w.spec.footprint()
         with self.cv:
             while not w.active:
+                need = w.spec.workspace_bytes() + (0 if w.resident else w.spec.resident_bytes())
                 if self.used + need <= self.budget:
                     self.used += need
                     self.max_used = max(self.max_used, self.used)
                     w.activate()
                     break
-                idle = [o for o in self.workers.values() if o.active and not o.busy and o.q.empty() and o is not w]
-                if idle:
-                    victim = min(idle, key=lambda o: o.last_used)
-                    victim.retire()
-                    self.used -= victim.spec.footprint()
+                idle = [o for o in self.workers.values()
+                        if o is not w and not o.busy and o.q.empty() and o.spec.prebuilt is None]
+                active_idle = [o for o in idle if o.active]
+                if active_idle:
+                    victim = min(active_idle, key=lambda o: o.last_used)
+                    victim.trim()
+                    self.used -= victim.spec.workspace_bytes()
+                    self.trims += 1
+                    continue
+                resident_idle = [o for o in idle if o.resident and not o.active]
+                if resident_idle:
+                    victim = min(resident_idle, key=lambda o: o.last_used)
+                    victim.close()
+                    self.used -= victim.spec.resident_bytes()
+                    self.closes += 1
                     continue
                 self.cv.wait(timeout=0.05)
 
@@ -245,7 +287,7 @@ class Server:
             w.q.put(None)
         for w in self.workers.values():
             w.thread.join(timeout=60)
-            w.retire()
+            w.close()
 
 
 def poisson_arrivals(rate_per_s: float, n: int, seed: int) -> np.ndarray:

@@ -137,3 +137,35 @@ def test_result_same_alone_and_in_mix(serving):
         op.close()
         assert np.linalg.norm(r["x"] - x) / np.linalg.norm(x) <= 10 * 1e-8 * 1e3
     srv.close()
+
+
+def test_trim_keeps_basis(serving):
+    """eig_op_trim gives an operator's workspace back and keeps its basis: the next solve
+    allocates the workspace again and deflates exactly as before."""
+    from paper_0707_0131_gb300.api import Basis, Op
+
+    spec = _specs(serving)[1]
+    op = Op(spec.gauge, spec.dims, spec.m_q, prec=32, max_rhs=4)
+    basis = Basis(op, 16)
+    for i in range(2):
+        b = fx.make_rhs(spec.dims, 9300 + i)[0].reshape(-1)
+        op.eigcg_solve(b, np.zeros_like(b), 4, 12, 1e-8, basis=basis)
+        basis.grow()
+    l = basis.size
+    th0, _ = basis.ritz(residuals=False)
+    B = np.stack([fx.make_rhs(spec.dims, 9400 + i)[0].reshape(-1) for i in range(4)])
+    X0 = np.zeros_like(B)
+    st0 = op.initcg_solve(B, X0, tol=1e-8, restart_tol=1e-6, basis=basis, k=4)
+    freed = op.trim()
+    assert freed > 4 * 12 * fx.volume(spec.dims) * 16  # at least the FP64 staging of k = 4
+    assert basis.size == l
+    th1, _ = basis.ritz(residuals=False)
+    assert np.array_equal(th0, th1)
+    X1 = np.zeros_like(B)
+    st1 = op.initcg_solve(B, X1, tol=1e-8, restart_tol=1e-6, basis=basis, k=4)
+    for r in range(4):
+        assert st1[r]["iters"] == st0[r]["iters"]
+        assert np.linalg.norm(X1[r] - X0[r]) / np.linalg.norm(X0[r]) < 1e-6
+        assert _check(spec, B[r], X1[r], 1e-8)
+    basis.close()
+    op.close()

@@ -1,6 +1,7 @@
-"""Host logic of the serving loop (no GPU): admission under the HBM budget retires the
-least recently used idle operator, waits while the others are busy, and the Poisson
-arrival generator and latency percentiles behave as stated."""
+"""Host logic of the serving loop (no GPU): admission under the HBM budget first takes
+workspaces back from idle operators (their bases stay), then closes the least recently
+used idle operator, waits while the others are busy, skips operators with queued
+requests, and the Poisson arrival generator and latency percentiles behave as stated."""
 import queue
 import threading
 import time
@@ -11,18 +12,27 @@ from paper_0707_0131_gb300 import serving
 
 
 class _Spec:
-    def __init__(self, key, nbytes):
+    def __init__(self, key, resident, workspace):
         self.key = key
-        self.nbytes = nbytes
+        self.res = resident
+        self.ws = workspace
+        self.prebuilt = None
+
+    def resident_bytes(self):
+        return self.res
+
+    def workspace_bytes(self):
+        return self.ws
 
     def footprint(self):
-        return self.nbytes
+        return self.res + self.ws
 
 
 class _FakeWorker:
-    def __init__(self, key, nbytes, last_used):
-        self.spec = _Spec(key, nbytes)
+    def __init__(self, key, resident, workspace, last_used):
+        self.spec = _Spec(key, resident, workspace)
         self.active = False
+        self.resident = False
         self.busy = False
         self.q = queue.Queue()
         self.last_used = last_used
@@ -30,11 +40,17 @@ class _FakeWorker:
 
     def activate(self):
         self.active = True
+        self.resident = True
         self.events.append("activate")
 
-    def retire(self):
+    def trim(self):
         self.active = False
-        self.events.append("retire")
+        self.events.append("trim")
+
+    def close(self):
+        self.active = False
+        self.resident = False
+        self.events.append("close")
 
 
 def _server(budget, workers):
@@ -43,21 +59,35 @@ def _server(budget, workers):
     return srv
 
 
-def test_admission_retires_least_recently_used_idle_operator():
-    a, b, c = _FakeWorker("a", 40, 1.0), _FakeWorker("b", 40, 2.0), _FakeWorker("c", 50, 3.0)
+def test_admission_trims_before_it_closes():
+    # resident 10 + workspace 30 each (c: 20 + 30), budget 100
+    a, b, c = _FakeWorker("a", 10, 30, 1.0), _FakeWorker("b", 10, 30, 2.0), _FakeWorker("c", 20, 30, 3.0)
     srv = _server(100, [a, b, c])
     srv._admit(a)
     srv._admit(b)
     assert srv.used == 80 and a.active and b.active
-    srv._admit(c)  # needs 50: the older idle operator (a) goes
-    assert a.events == ["activate", "retire"] and b.active and c.active
-    assert srv.used == 90 and srv.max_used == 90
+    srv._admit(c)  # needs 50: the older idle operator (a) gives its workspace back, keeps its basis
+    assert a.events == ["activate", "trim"] and a.resident and b.active and c.active
+    assert srv.used == 100 and srv.max_used == 100 and srv.trims == 1 and srv.closes == 0
     srv._admit(c)  # already active: nothing changes
-    assert srv.used == 90
+    assert srv.used == 100
+    # a again: only its workspace is needed (30); b and c give theirs back in LRU order
+    b.last_used, c.last_used = 4.0, 5.0
+    srv._admit(a)
+    assert a.active and b.events[-1] == "trim" and c.active and srv.used == 100
+
+
+def test_admission_closes_when_trimming_is_not_enough():
+    a, b = _FakeWorker("a", 50, 30, 1.0), _FakeWorker("b", 40, 30, 2.0)
+    srv = _server(100, [a, b])
+    srv._admit(a)  # 80
+    srv._admit(b)  # needs 70: trimming a leaves 50 + 70 > 100, so a is closed as well
+    assert a.events == ["activate", "trim", "close"] and not a.resident
+    assert b.active and srv.used == 70 and srv.trims == 1 and srv.closes == 1
 
 
 def test_admission_waits_for_busy_operators():
-    a, b = _FakeWorker("a", 60, 1.0), _FakeWorker("b", 60, 2.0)
+    a, b = _FakeWorker("a", 20, 40, 1.0), _FakeWorker("b", 20, 40, 2.0)
     srv = _server(100, [a, b])
     srv._admit(a)
     a.busy = True
@@ -70,20 +100,20 @@ def test_admission_waits_for_busy_operators():
     t = threading.Thread(target=release)
     t.start()
     t0 = time.perf_counter()
-    srv._admit(b)  # a is busy: b waits until a is idle, then a is retired
+    srv._admit(b)  # a is busy: b waits until a is idle, then a gives its workspace back
     t.join()
     assert time.perf_counter() - t0 >= 0.15
-    assert b.active and not a.active and srv.used == 60
+    assert b.active and not a.active and a.resident and srv.used == 80
 
 
 def test_admission_skips_operators_with_queued_requests():
-    a, b, c = _FakeWorker("a", 50, 1.0), _FakeWorker("b", 50, 2.0), _FakeWorker("c", 50, 3.0)
-    srv = _server(100, [a, b, c])
+    a, b, c = _FakeWorker("a", 10, 40, 1.0), _FakeWorker("b", 10, 40, 2.0), _FakeWorker("c", 10, 40, 3.0)
+    srv = _server(110, [a, b, c])
     srv._admit(a)
     srv._admit(b)
-    a.q.put("pending request")  # a is idle but has work waiting: b is retired instead
+    a.q.put("pending request")  # a is idle but has work waiting: b gives its workspace back
     srv._admit(c)
-    assert a.active and not b.active and c.active
+    assert a.active and not b.active and b.resident and c.active
 
 
 def test_poisson_arrivals_and_percentiles():
