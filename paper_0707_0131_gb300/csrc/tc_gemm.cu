@@ -114,6 +114,26 @@ __device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t adesc, uint64_
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
         : "memory");
 }
+// the same with A read from tensor memory (M = 128 rows in the 128 lanes, one 32-bit
+// column per K element; a K step of 8 advances the address by 8 columns)
+__device__ __forceinline__ void mma_tf32_ts(uint32_t dtmem, uint32_t atmem, uint64_t bdesc, uint32_t idesc, int accum) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(dtmem),
+        "r"(atmem), "l"(bdesc), "r"(idesc), "r"(accum)
+        : "memory");
+}
+// 32 consecutive TMEM columns of this thread's lane (its warp's lane quarter) from registers
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const float *x) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,"
+        "%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};\n" ::"r"(taddr),
+        "f"(x[0]), "f"(x[1]), "f"(x[2]), "f"(x[3]), "f"(x[4]), "f"(x[5]), "f"(x[6]), "f"(x[7]), "f"(x[8]), "f"(x[9]),
+        "f"(x[10]), "f"(x[11]), "f"(x[12]), "f"(x[13]), "f"(x[14]), "f"(x[15]), "f"(x[16]), "f"(x[17]), "f"(x[18]),
+        "f"(x[19]), "f"(x[20]), "f"(x[21]), "f"(x[22]), "f"(x[23]), "f"(x[24]), "f"(x[25]), "f"(x[26]), "f"(x[27]),
+        "f"(x[28]), "f"(x[29]), "f"(x[30]), "f"(x[31])
+        : "memory");
+}
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(sa(bar))
                  : "memory");
@@ -432,10 +452,11 @@ __global__ void k_tc_reduce(const double *partials, int grid, int MT, int N, int
 // stays at FP32-product accuracy without draining.
 // ------------------------------------------------------------------------------------
 template <int N>
-struct AyStages {
-    static constexpr int value = N <= 32 ? 6 : 5;  // staging ring depth (bulk copies in flight)
+struct AyStages {  // staging ring depth (copies in flight): 208 KB of shared memory with the B buffers
+    static constexpr int value = N == 16 ? 12 : (N == 32 ? 11 : 9);
 };
-constexpr int AY_NOP = 3;         // operand (A hi/lo + B hi/lo) buffers
+constexpr int AY_NOP = 4;         // operand buffers: A hi / lo in TMEM, B hi / lo in shared memory
+constexpr int AY_TCOLS = 512;     // TMEM columns: 2 accumulators, then AY_NOP x (32 A_hi + 32 A_lo)
 constexpr int AY_COLS = 16;       // basis columns per K chunk
 constexpr int AY_THREADS = TC_THREADS;
 
@@ -457,6 +478,9 @@ struct AyArgs {
     // B operand of every K chunk, split into TF32 hi and lo and laid out as the MMA reads
     // it (K-major, 128-byte swizzle): [chunk][hi, lo][N / 8 KB], built once per launch
     const unsigned char *Bpre;
+    // A's columns evenly spaced (no aoff): one 2D TMA copy per job through the kernel's
+    // tensor map instead of one bulk copy per column segment
+    int tma;
 };
 
 // Builds AyArgs::Bpre from Y: row r = 2c + e of chunk kc's B tile holds, at K position
@@ -489,51 +513,54 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned by
         : "memory");
 }
 
-// Same roles as k_tc_ahb: warp 0 issues the bulk copies, warp 1 the MMAs, warps 2..9
-// transpose / split the staged columns, build Yt and write the outputs of each tile
-// one chunk after its last MMA (two TMEM accumulators alternate between tiles).
+// Roles: warp 0 issues the bulk copies, warp 1 the MMAs; warps 2..5 and 6..9 are two
+// worker groups that take alternate jobs (a job = one K chunk of one tile): transpose and
+// split the staged columns, copy in the chunk's B tile, and write the outputs of a tile
+// whose last job was theirs one of their jobs later (two TMEM accumulators alternate
+// between tiles).
 template <int N>
-__global__ void __launch_bounds__(AY_THREADS, 1) k_tc_ay(const AyArgs a) {
+__global__ void __launch_bounds__(AY_THREADS, 1) k_tc_ay(const __grid_constant__ CUtensorMap amap, const AyArgs a) {
     constexpr int AY_NSTG = AyStages<N>::value;
     extern __shared__ __align__(1024) unsigned char sm_raw[];
     unsigned char *base = sm_raw + ((1024 - (sa(sm_raw) & 1023)) & 1023);
     constexpr uint32_t stg_bytes = AY_COLS * TM * 8;            // 16 KB: [16 columns][128 rows] float2
-    constexpr uint32_t a_bytes = TM * KT * 4;                    // 16 KB: one of A_hi / A_lo
     constexpr uint32_t b_bytes = (uint32_t)(N / 8) * 1024;
-    constexpr uint32_t op_bytes = 2 * a_bytes + 2 * b_bytes;     // A_hi, A_lo, B_hi, B_lo
+    constexpr uint32_t op_bytes = 2 * b_bytes;                   // B_hi, B_lo (A is in TMEM)
     constexpr uint32_t ACOLS = N <= 32 ? 32 : 64;                 // TMEM columns per accumulator
+    constexpr uint32_t AC0 = 2 * ACOLS;                          // first A column in TMEM
+    static_assert(AC0 + AY_NOP * 2 * KT <= AY_TCOLS, "TMEM columns");
     unsigned char *stg = base;
     unsigned char *ops = base + AY_NSTG * stg_bytes;
     __shared__ __align__(8) uint64_t stg_full[AY_NSTG], stg_free[AY_NSTG], op_ready[AY_NOP], op_free[AY_NOP],
         acc_full[2], acc_empty[2], done;
     __shared__ uint32_t tmem_base;
     __shared__ volatile int abort_flag;
-    __shared__ int n_issued, n_consumed;
+    __shared__ int n_issued;
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     const int my_tiles = a.mtiles > (int)blockIdx.x ? (a.mtiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     const int njobs = my_tiles * a.nch;
     if (t == 0) {
+        // one worker group (WORKERS / 2 warps) reads, fills and drains each job or tile
         for (int i = 0; i < AY_NSTG; i++) {
             mbar_init(&stg_full[i], 1);
-            mbar_init(&stg_free[i], WORKERS);
+            mbar_init(&stg_free[i], WORKERS / 2);
         }
         for (int i = 0; i < AY_NOP; i++) {
-            mbar_init(&op_ready[i], WORKERS);
+            mbar_init(&op_ready[i], WORKERS / 2);
             mbar_init(&op_free[i], 1);
         }
         for (int i = 0; i < 2; i++) {
             mbar_init(&acc_full[i], 1);
-            mbar_init(&acc_empty[i], WORKERS);
+            mbar_init(&acc_empty[i], WORKERS / 2);
         }
         mbar_init(&done, 1);
         abort_flag = 0;
         n_issued = 0;
-        n_consumed = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(sa(&tmem_base)),
-                     "r"(2 * ACOLS)
+                     "r"(AY_TCOLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
     }
@@ -547,7 +574,7 @@ __global__ void __launch_bounds__(AY_THREADS, 1) k_tc_ay(const AyArgs a) {
     };
 
     if (warp == 0) {
-        // ---------------- producer: bulk copies of the column segments ----------------
+        // ---------------- producer: copies of the column segments ----------------
         if (lane == 0) {
             int j = 0;
             for (; j < njobs && !abort_flag; j++) {
@@ -564,6 +591,15 @@ __global__ void __launch_bounds__(AY_THREADS, 1) k_tc_ay(const AyArgs a) {
                 const long n0 = (long)job_tile(j) * TM;
                 const long rows = min((long)TM, a.nrows - n0);
                 const int c0 = kc * AY_COLS, nc = min(AY_COLS, a.nA - c0);
+                if (a.tma) {
+                    // box of 2 TM floats x AY_COLS columns, landing as [column][row] float2 like
+                    // the bulk copies; rows and columns past the ends are filled with zeros and
+                    // still counted, so the transaction is always the whole box.  x = 2 n0 is a
+                    // multiple of 256 floats (1 KB).
+                    mbar_expect_tx(&stg_full[s], stg_bytes);
+                    tma_load_2d(stg + s * stg_bytes, &amap, (int)(2 * n0), c0, &stg_full[s]);
+                    continue;
+                }
                 mbar_expect_tx(&stg_full[s], (unsigned)(nc * rows * 8));
                 for (int c = 0; c < nc; c++) {
                     const float2 *col = a.A + (a.aoff ? a.aoff[c0 + c] : (long)(c0 + c) * a.acol);
@@ -587,16 +623,17 @@ __global__ void __launch_bounds__(AY_THREADS, 1) k_tc_ay(const AyArgs a) {
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-                unsigned char *Ahi = ops + o * op_bytes, *Alo = Ahi + a_bytes;
-                unsigned char *Bhi = Ahi + 2 * a_bytes, *Blo = Bhi + b_bytes;
+                unsigned char *Bhi = ops + o * op_bytes, *Blo = Bhi + b_bytes;
                 const uint32_t d = tmem + (uint32_t)((ti & 1) * ACOLS);
-                const uint64_t ah0 = sdesc(sa(Ahi)), al0 = sdesc(sa(Alo)), bh0 = sdesc(sa(Bhi)), bl0 = sdesc(sa(Blo));
+                const uint32_t ahi = tmem + AC0 + (uint32_t)(o * 2 * KT), alo = ahi + KT;
+                const uint64_t bh0 = sdesc(sa(Bhi)), bl0 = sdesc(sa(Blo));
 #pragma unroll
                 for (int ks = 0; ks < KT / 8; ks++) {
-                    const uint64_t o = 2 * ks;  // 32 bytes along the swizzled row
-                    mma_tf32(d, ah0 + o, bh0 + o, idesc, (kc > 0 || ks > 0) ? 1 : 0);
-                    mma_tf32(d, ah0 + o, bl0 + o, idesc, 1);
-                    mma_tf32(d, al0 + o, bh0 + o, idesc, 1);
+                    const uint64_t bo = 2 * ks;  // 32 bytes along the swizzled row of B
+                    const uint32_t ao = 8 * ks;  // 8 TMEM columns of A
+                    mma_tf32_ts(d, ahi + ao, bh0 + bo, idesc, (kc > 0 || ks > 0) ? 1 : 0);
+                    mma_tf32_ts(d, ahi + ao, bl0 + bo, idesc, 1);
+                    mma_tf32_ts(d, alo + ao, bh0 + bo, idesc, 1);
                 }
                 mma_commit(&op_free[o]);
                 if (kc == a.nch - 1) mma_commit(&acc_full[ti & 1]);
@@ -604,8 +641,21 @@ __global__ void __launch_bounds__(AY_THREADS, 1) k_tc_ay(const AyArgs a) {
             mma_commit(&done);
         }
     } else {
-        // ---------------- workers ----------------
-        const int wt = t - 64, quarter = warp & 3, half = (warp - 2) >> 2;
+        // ---------------- workers: two groups of four warps on alternate jobs ----------------
+        // Each group covers the four TMEM lane quarters, so a group splits whole tiles and
+        // writes whole outputs on its own; while one group waits (a barrier, its B loads, an
+        // epilogue) the other splits the next job.
+        const int grp = (warp - 2) >> 2, quarter = warp & 3;
+        const int n = (t - 64) & (TM - 1);  // this thread's share of the B copy
+        const int rt = quarter * 32 + lane;  // the tile row (TMEM lane) this thread splits
+        constexpr int NB4 = (int)(2 * b_bytes / 16) / TM;  // float4 of B (hi, lo) per thread per job
+        static_assert(NB4 * TM * 16 == (int)(2 * b_bytes), "B operand split evenly over a group");
+        float4 bnext[NB4];
+        auto load_b = [&](int j) {  // B of job j into registers, one job of this group ahead
+            const float4 *src = reinterpret_cast<const float4 *>(a.Bpre + (size_t)(j % a.nch) * 2 * b_bytes);
+#pragma unroll
+            for (int i = 0; i < NB4; i++) bnext[i] = __ldg(src + n + TM * i);
+        };
         // outputs of tile ti (rows n0 ..), from accumulator ti & 1; warp-uniform
         auto epilogue = [&](int ti) {
             const bool ok = __all_sync(0xffffffffu, mbar_wait(&acc_full[ti & 1], (ti >> 1) & 1));
@@ -614,55 +664,64 @@ __global__ void __launch_bounds__(AY_THREADS, 1) k_tc_ay(const AyArgs a) {
                 return false;
             }
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-            constexpr int HC = N / 2;
-            uint32_t v[HC];
-            const uint32_t addr = tmem + (uint32_t)((ti & 1) * ACOLS) + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * HC);
-            if constexpr (HC == 8) {
-                asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
-                             : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-                               "=r"(v[7])
-                             : "r"(addr)
-                             : "memory");
-            } else {
+            uint32_t v[N];
+            const uint32_t addr = tmem + (uint32_t)((ti & 1) * ACOLS) + ((uint32_t)(quarter * 32) << 16);
 #pragma unroll
-                for (int c0 = 0; c0 < HC; c0 += 16)
-                    asm volatile(
-                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
-                        "%15}, [%16];\n"
-                        : "=r"(v[c0 + 0]), "=r"(v[c0 + 1]), "=r"(v[c0 + 2]), "=r"(v[c0 + 3]), "=r"(v[c0 + 4]),
-                          "=r"(v[c0 + 5]), "=r"(v[c0 + 6]), "=r"(v[c0 + 7]), "=r"(v[c0 + 8]), "=r"(v[c0 + 9]),
-                          "=r"(v[c0 + 10]), "=r"(v[c0 + 11]), "=r"(v[c0 + 12]), "=r"(v[c0 + 13]), "=r"(v[c0 + 14]),
-                          "=r"(v[c0 + 15])
-                        : "r"(addr + c0)
-                        : "memory");
-            }
+            for (int c0 = 0; c0 < N; c0 += 16)
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+                    "%15}, [%16];\n"
+                    : "=r"(v[c0 + 0]), "=r"(v[c0 + 1]), "=r"(v[c0 + 2]), "=r"(v[c0 + 3]), "=r"(v[c0 + 4]),
+                      "=r"(v[c0 + 5]), "=r"(v[c0 + 6]), "=r"(v[c0 + 7]), "=r"(v[c0 + 8]), "=r"(v[c0 + 9]),
+                      "=r"(v[c0 + 10]), "=r"(v[c0 + 11]), "=r"(v[c0 + 12]), "=r"(v[c0 + 13]), "=r"(v[c0 + 14]),
+                      "=r"(v[c0 + 15])
+                    : "r"(addr + c0)
+                    : "memory");
             asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
             asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
             __syncwarp();
             if (lane == 0) mbar_arrive(&acc_empty[ti & 1]);
-            const long n = (long)((int)blockIdx.x + ti * (int)gridDim.x) * TM + quarter * 32 + lane;
-            if (n < a.nrows) {
+            const long row = (long)((int)blockIdx.x + ti * (int)gridDim.x) * TM + quarter * 32 + lane;
+            if (row < a.nrows) {
+                // columns in groups of 8: a group's addresses and (beta != 0) old values are all
+                // read before its first store, so that those loads overlap instead of each
+                // waiting behind the previous store
+                constexpr int CG = 8;
 #pragma unroll
-                for (int q = 0; q < HC / 2; q++) {
-                    const int c = half * (HC / 2) + q;
-                    if (c < a.k) {
-                        float2 *op = a.ooff ? a.Out + a.ooff[c] + n
-                                            : a.Out + ((n >> 1) * a.oki + c % a.oki) * 2 + (n & 1) + (long)(c / a.oki) * a.ocol;
-                        float2 r = make_float2(__uint_as_float(v[2 * q]), __uint_as_float(v[2 * q + 1]));
-                        if (a.beta != 0.f) {
-                            const float2 old = *op;
-                            r.x += a.beta * old.x;
-                            r.y += a.beta * old.y;
-                        }
-                        *op = r;
+                for (int c0 = 0; c0 < N / 2; c0 += CG) {
+                    float2 *op[CG];
+#pragma unroll
+                    for (int q = 0; q < CG; q++) {
+                        const int c = c0 + q;
+                        op[q] = c >= a.k ? nullptr
+                                : a.ooff ? a.Out + a.ooff[c] + row
+                                         : a.Out + ((row >> 1) * a.oki + c % a.oki) * 2 + (row & 1) + (long)(c / a.oki) * a.ocol;
                     }
+                    float2 r[CG];
+#pragma unroll
+                    for (int q = 0; q < CG; q++)
+                        r[q] = make_float2(__uint_as_float(v[2 * (c0 + q)]), __uint_as_float(v[2 * (c0 + q) + 1]));
+                    if (a.beta != 0.f) {
+                        float2 old[CG];
+#pragma unroll
+                        for (int q = 0; q < CG; q++) old[q] = op[q] ? *op[q] : make_float2(0.f, 0.f);
+#pragma unroll
+                        for (int q = 0; q < CG; q++) {
+                            r[q].x += a.beta * old[q].x;
+                            r[q].y += a.beta * old[q].y;
+                        }
+                    }
+#pragma unroll
+                    for (int q = 0; q < CG; q++)
+                        if (op[q]) *op[q] = r[q];
                 }
             }
             return true;
         };
-        int j = 0, pending = -1;  // tile whose outputs are still to be written
+        int pending = -1;  // tile whose outputs are still to be written (its last job was this group's)
         bool ok = true;
-        for (; j < njobs && ok && !abort_flag; j++) {
+        if (grp < njobs) load_b(grp);
+        for (int j = grp; j < njobs && ok && !abort_flag; j += 2) {
             const int s = j % AY_NSTG, o = j % AY_NOP, kc = j % a.nch;
             const long n0 = (long)job_tile(j) * TM;
             const long rows = min((long)TM, a.nrows - n0);
@@ -675,64 +734,61 @@ __global__ void __launch_bounds__(AY_THREADS, 1) k_tc_ay(const AyArgs a) {
                 fail(16);
                 break;
             }
-            unsigned char *Ahi = ops + o * op_bytes, *Alo = Ahi + a_bytes;
-            unsigned char *Bhi = Ahi + 2 * a_bytes, *Blo = Bhi + b_bytes;
+            unsigned char *Bhi = ops + o * op_bytes;
             {
-                // transpose + split: worker thread (row n, half h) takes columns 8h .. 8h + 7 of its row
-                const int n = wt & (TM - 1), h = wt >> 7;
+                // transpose + split: thread rt takes the 16 staged columns of row rt (K positions
+                // 2c, 2c + 1 for column c) and writes hi and lo to 32 TMEM columns each of its lane
                 const float2 *sg = reinterpret_cast<const float2 *>(stg + s * stg_bytes);
-                float v[16];
+                float hv[KT], lv[KT];
 #pragma unroll
-                for (int q = 0; q < 8; q++) {
-                    const int c = 8 * h + q;
+                for (int c = 0; c < AY_COLS; c++) {
                     float2 x = make_float2(0.f, 0.f);
-                    if (c < nc && n < rows) x = sg[c * TM + n];
-                    v[2 * q] = x.x;
-                    v[2 * q + 1] = x.y;
+                    if (c < nc && rt < rows) x = sg[c * TM + rt];
+                    hv[2 * c] = hi_tf32(x.x);
+                    hv[2 * c + 1] = hi_tf32(x.y);
+                    lv[2 * c] = x.x - hv[2 * c];
+                    lv[2 * c + 1] = x.y - hv[2 * c + 1];
                 }
-#pragma unroll
-                for (int q4 = 0; q4 < 4; q4++) {  // K positions 16h + 4 q4 .. + 3
-                    float hv[4], lv[4];
-#pragma unroll
-                    for (int e = 0; e < 4; e++) {
-                        hv[e] = hi_tf32(v[4 * q4 + e]);
-                        lv[e] = v[4 * q4 + e] - hv[e];
-                    }
-                    const uint32_t off = sw128(n, 16 * h + 4 * q4);
-                    *reinterpret_cast<float4 *>(Ahi + off) = make_float4(hv[0], hv[1], hv[2], hv[3]);
-                    *reinterpret_cast<float4 *>(Alo + off) = make_float4(lv[0], lv[1], lv[2], lv[3]);
-                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&stg_free[s]);  // the staging slot has been read
+                // the MMAs that read this buffer's previous contents have completed (op_free)
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) + AC0 + (uint32_t)(o * 2 * KT);
+                tmem_st32(ta, hv);
+                tmem_st32(ta + KT, lv);
+                asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
             }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&stg_free[s]);  // the staging slot has been read
-            // B = Yt for this chunk: a copy of the tiles k_ay_prep_b built (hi, then lo; the two
-            // are contiguous in the operand buffer as in Bpre)
+            // B = Yt for this chunk (hi, then lo, contiguous as in Bpre), from the registers
+            // loaded one job ahead; then the loads for this group's next job
             {
-                const float4 *src = reinterpret_cast<const float4 *>(a.Bpre + (size_t)kc * 2 * b_bytes);
                 float4 *dst = reinterpret_cast<float4 *>(Bhi);
-                for (int i = wt; i < (int)(2 * b_bytes / 16); i += 32 * WORKERS) dst[i] = __ldg(src + i);
+#pragma unroll
+                for (int i = 0; i < NB4; i++) dst[n + TM * i] = bnext[i];
             }
+            if (j + 2 < njobs) load_b(j + 2);
             asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
             __syncwarp();
             if (lane == 0) mbar_arrive(&op_ready[o]);
-            // the previous tile's outputs, one chunk after its last MMA was issued
+            // this group's previous tile, one of its jobs after that tile's last MMA was issued
             if (pending >= 0) {
                 ok = epilogue(pending);
                 pending = -1;
             }
             if (kc == a.nch - 1) pending = j / a.nch;
         }
-        if (wt == 0) n_consumed = j;
         if (ok && pending >= 0 && !abort_flag) epilogue(pending);
     }
     __syncthreads();
+    // after an abort: let the copies still in flight land (the last job issued on each
+    // staging slot; a slot's earlier phases completed before it was refilled)
     if (t == 0)
-        for (int j = n_consumed; j < n_issued; j++) mbar_wait(&stg_full[j % AY_NSTG], (j / AY_NSTG) & 1);
+        for (int j = max(0, n_issued - AY_NSTG); j < n_issued; j++) mbar_wait(&stg_full[j % AY_NSTG], (j / AY_NSTG) & 1);
     if (!mbar_wait(&done, 0)) atomicExch(a.err, 17);
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(2 * ACOLS) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(AY_TCOLS) : "memory");
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
@@ -870,6 +926,21 @@ cudaError_t launch_tc_ay(const ColSet &A, const double *Y, const ColSet &Out, do
     a.nch = (A.ncols + AY_COLS - 1) / AY_COLS;
     a.err = err;
     a.Bpre = static_cast<const unsigned char *>(bscratch);
+    a.tma = 0;
+    CUtensorMap amap;
+    memset(&amap, 0, sizeof(amap));
+    if (!A.col_off && get_encoder() == cudaSuccess) {
+        // A as a 2D FP32 tensor: 2 nrows floats per column (x), nA columns (y) col_stride
+        // complex apart; the box is one job's staging slot (2 TM floats x AY_COLS columns)
+        const cuuint64_t dims[2] = {(cuuint64_t)(2 * nrows), (cuuint64_t)A.ncols};
+        const cuuint64_t strides[1] = {(cuuint64_t)A.col_stride * 8};
+        const cuuint32_t box[2] = {2 * TM, AY_COLS};
+        const cuuint32_t estr[2] = {1, 1};
+        const CUresult r = g_encode(&amap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(A.base), dims, strides,
+                                    box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        a.tma = r == CUDA_SUCCESS ? 1 : 0;
+    }
     const int N = 2 * Out.ncols <= 16 ? 16 : (2 * Out.ncols <= 32 ? 32 : 64);
     if ((size_t)a.nch * 2 * (size_t)(N / 8) * 1024 > TC_AY_SCRATCH) return cudaErrorInvalidValue;
     {
@@ -882,12 +953,11 @@ cudaError_t launch_tc_ay(const ColSet &A, const double *Y, const ColSet &Out, do
     }
     int grid = device_sm_count();
     if (grid > a.mtiles) grid = a.mtiles;
-    const int nstg = N <= 32 ? 6 : 5;  // AyStages<N>
-    const size_t smem =
-        nstg * (size_t)(AY_COLS * TM * 8) + AY_NOP * (2 * (size_t)(TM * KT * 4) + 2 * (size_t)(N / 8) * 1024) + 1024;
+    const int nstg = N == 16 ? 12 : (N == 32 ? 11 : 9);  // AyStages<N>
+    const size_t smem = nstg * (size_t)(AY_COLS * TM * 8) + AY_NOP * 2 * (size_t)(N / 8) * 1024 + 1024;
     auto go = [&](auto kern) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        kern<<<grid, AY_THREADS, smem, s>>>(a);
+        kern<<<grid, AY_THREADS, smem, s>>>(amap, a);
     };
     if (N == 16) go(k_tc_ay<16>);
     else if (N == 32) go(k_tc_ay<32>);
