@@ -63,6 +63,17 @@ __device__ __forceinline__ bool mbar_try(uint64_t *b, unsigned phase) {
         : "memory");
     return ok != 0;
 }
+// non-blocking test of the same phase (no suspension, for the fast path of a wait that
+// usually finds the phase complete)
+__device__ __forceinline__ bool mbar_test(uint64_t *b, unsigned phase) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(sa(b)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
 __device__ __forceinline__ uint64_t gtimer() {
     uint64_t t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -526,7 +537,9 @@ __global__ void __launch_bounds__(AY_THREADS, 1) k_tc_ay(const __grid_constant__
     constexpr uint32_t stg_bytes = AY_COLS * TM * 8;            // 16 KB: [16 columns][128 rows] float2
     constexpr uint32_t b_bytes = (uint32_t)(N / 8) * 1024;
     constexpr uint32_t op_bytes = 2 * b_bytes;                   // B_hi, B_lo (A is in TMEM)
-    constexpr uint32_t ACOLS = N <= 32 ? 32 : 64;                 // TMEM columns per accumulator
+    // one accumulator holds A B_hi in its first N columns and A B_lo in the next N (B_lo's
+    // rows follow B_hi's in shared memory, so one MMA of width 2N takes both)
+    constexpr uint32_t ACOLS = 2 * N;                            // TMEM columns per accumulator
     constexpr uint32_t AC0 = 2 * ACOLS;                          // first A column in TMEM
     static_assert(AC0 + AY_NOP * 2 * KT <= AY_TCOLS, "TMEM columns");
     unsigned char *stg = base;
@@ -575,12 +588,17 @@ __global__ void __launch_bounds__(AY_THREADS, 1) k_tc_ay(const __grid_constant__
 
     if (warp == 0) {
         // ---------------- producer: copies of the column segments ----------------
+        // (one thread: slot, chunk and row position advance by counters, with no divisions
+        // per job; a barrier that is already complete is taken without a call)
         if (lane == 0) {
-            int j = 0;
-            for (; j < njobs && !abort_flag; j++) {
-                const int s = j % AY_NSTG, kc = j % a.nch;
-                if (j >= AY_NSTG) {
-                    if (!mbar_wait(&stg_free[s], ((j / AY_NSTG) - 1) & 1)) {
+            int j = 0, s = 0, kc = 0;
+            unsigned lap = 0;  // j / AY_NSTG
+            long n0 = (long)blockIdx.x * TM;
+            for (; j < njobs; j++) {
+                if (kc == 0 && abort_flag) break;
+                if (lap > 0) {
+                    const unsigned par = (lap - 1) & 1;
+                    if (!mbar_test(&stg_free[s], par) && !mbar_wait(&stg_free[s], par)) {
                         fail(11);
                         break;
                     }
@@ -588,9 +606,7 @@ __global__ void __launch_bounds__(AY_THREADS, 1) k_tc_ay(const __grid_constant__
                     // through the async proxy
                     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
                 }
-                const long n0 = (long)job_tile(j) * TM;
-                const long rows = min((long)TM, a.nrows - n0);
-                const int c0 = kc * AY_COLS, nc = min(AY_COLS, a.nA - c0);
+                const int c0 = kc * AY_COLS;
                 if (a.tma) {
                     // box of 2 TM floats x AY_COLS columns, landing as [column][row] float2 like
                     // the bulk copies; rows and columns past the ends are filled with zeros and
@@ -598,12 +614,22 @@ __global__ void __launch_bounds__(AY_THREADS, 1) k_tc_ay(const __grid_constant__
                     // multiple of 256 floats (1 KB).
                     mbar_expect_tx(&stg_full[s], stg_bytes);
                     tma_load_2d(stg + s * stg_bytes, &amap, (int)(2 * n0), c0, &stg_full[s]);
-                    continue;
+                } else {
+                    const long rows = min((long)TM, a.nrows - n0);
+                    const int nc = min(AY_COLS, a.nA - c0);
+                    mbar_expect_tx(&stg_full[s], (unsigned)(nc * rows * 8));
+                    for (int c = 0; c < nc; c++) {
+                        const float2 *col = a.A + (a.aoff ? a.aoff[c0 + c] : (long)(c0 + c) * a.acol);
+                        bulk_g2s(stg + s * stg_bytes + c * TM * 8, col + n0, (unsigned)(rows * 8), &stg_full[s]);
+                    }
                 }
-                mbar_expect_tx(&stg_full[s], (unsigned)(nc * rows * 8));
-                for (int c = 0; c < nc; c++) {
-                    const float2 *col = a.A + (a.aoff ? a.aoff[c0 + c] : (long)(c0 + c) * a.acol);
-                    bulk_g2s(stg + s * stg_bytes + c * TM * 8, col + n0, (unsigned)(rows * 8), &stg_full[s]);
+                if (++s == AY_NSTG) {
+                    s = 0;
+                    lap++;
+                }
+                if (++kc == a.nch) {
+                    kc = 0;
+                    n0 += (long)gridDim.x * TM;
                 }
             }
             n_issued = j;
@@ -611,32 +637,47 @@ __global__ void __launch_bounds__(AY_THREADS, 1) k_tc_ay(const __grid_constant__
     } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
-            const uint32_t idesc = idesc_tf32(TM, N);
-            for (int j = 0; j < njobs && !abort_flag; j++) {
-                const int o = j % AY_NOP, kc = j % a.nch, ti = j / a.nch;
-                if (!mbar_wait(&op_ready[o], (j / AY_NOP) & 1)) {
+            const uint32_t idesc = idesc_tf32(TM, 2 * N);
+            const uint64_t bdesc0 = sdesc(sa(ops));  // buffer o's B adds (o op_bytes) >> 4
+            int o = 0, kc = 0, ti = 0;
+            unsigned lap = 0;  // j / AY_NOP
+            for (int j = 0; j < njobs; j++) {
+                if (kc == 0 && abort_flag) break;
+                const unsigned par = lap & 1;
+                if (!mbar_test(&op_ready[o], par) && !mbar_wait(&op_ready[o], par)) {
                     fail(12);
                     break;
                 }
-                if (kc == 0 && ti >= 2 && !mbar_wait(&acc_empty[ti & 1], ((ti >> 1) - 1) & 1)) {
-                    fail(13);
-                    break;
+                if (kc == 0 && ti >= 2) {
+                    const unsigned pe = ((ti >> 1) - 1) & 1;
+                    if (!mbar_test(&acc_empty[ti & 1], pe) && !mbar_wait(&acc_empty[ti & 1], pe)) {
+                        fail(13);
+                        break;
+                    }
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-                unsigned char *Bhi = ops + o * op_bytes, *Blo = Bhi + b_bytes;
                 const uint32_t d = tmem + (uint32_t)((ti & 1) * ACOLS);
                 const uint32_t ahi = tmem + AC0 + (uint32_t)(o * 2 * KT), alo = ahi + KT;
-                const uint64_t bh0 = sdesc(sa(Bhi)), bl0 = sdesc(sa(Blo));
+                const uint64_t b0 = bdesc0 + (uint64_t)(((uint32_t)o * op_bytes) >> 4);  // B_hi rows, then B_lo rows
+                // per K step: A_hi [B_hi B_lo] + A_lo [B_hi B_lo], two MMAs of width 2N (the
+                // lo x lo term is below FP32 rounding and harmless)
 #pragma unroll
                 for (int ks = 0; ks < KT / 8; ks++) {
                     const uint64_t bo = 2 * ks;  // 32 bytes along the swizzled row of B
                     const uint32_t ao = 8 * ks;  // 8 TMEM columns of A
-                    mma_tf32_ts(d, ahi + ao, bh0 + bo, idesc, (kc > 0 || ks > 0) ? 1 : 0);
-                    mma_tf32_ts(d, ahi + ao, bl0 + bo, idesc, 1);
-                    mma_tf32_ts(d, alo + ao, bh0 + bo, idesc, 1);
+                    mma_tf32_ts(d, ahi + ao, b0 + bo, idesc, (kc > 0 || ks > 0) ? 1 : 0);
+                    mma_tf32_ts(d, alo + ao, b0 + bo, idesc, 1);
                 }
                 mma_commit(&op_free[o]);
                 if (kc == a.nch - 1) mma_commit(&acc_full[ti & 1]);
+                if (++o == AY_NOP) {
+                    o = 0;
+                    lap++;
+                }
+                if (++kc == a.nch) {
+                    kc = 0;
+                    ti++;
+                }
             }
             mma_commit(&done);
         }
@@ -667,7 +708,8 @@ __global__ void __launch_bounds__(AY_THREADS, 1) k_tc_ay(const __grid_constant__
             uint32_t v[N];
             const uint32_t addr = tmem + (uint32_t)((ti & 1) * ACOLS) + ((uint32_t)(quarter * 32) << 16);
 #pragma unroll
-            for (int c0 = 0; c0 < N; c0 += 16)
+            for (int c0 = 0; c0 < N; c0 += 16) {
+                uint32_t w[16];  // the B_lo half of the same 16 columns
                 asm volatile(
                     "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
                     "%15}, [%16];\n"
@@ -677,7 +719,18 @@ __global__ void __launch_bounds__(AY_THREADS, 1) k_tc_ay(const __grid_constant__
                       "=r"(v[c0 + 15])
                     : "r"(addr + c0)
                     : "memory");
-            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+                    "%15}, [%16];\n"
+                    : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]), "=r"(w[6]), "=r"(w[7]),
+                      "=r"(w[8]), "=r"(w[9]), "=r"(w[10]), "=r"(w[11]), "=r"(w[12]), "=r"(w[13]), "=r"(w[14]),
+                      "=r"(w[15])
+                    : "r"(addr + N + c0)
+                    : "memory");
+                asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+                for (int q = 0; q < 16; q++) v[c0 + q] = __float_as_uint(__uint_as_float(v[c0 + q]) + __uint_as_float(w[q]));
+            }
             asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
             __syncwarp();
             if (lane == 0) mbar_arrive(&acc_empty[ti & 1]);
@@ -726,11 +779,11 @@ __global__ void __launch_bounds__(AY_THREADS, 1) k_tc_ay(const __grid_constant__
             const long n0 = (long)job_tile(j) * TM;
             const long rows = min((long)TM, a.nrows - n0);
             const int nc = min(AY_COLS, a.nA - kc * AY_COLS);
-            if (!__all_sync(0xffffffffu, mbar_wait(&stg_full[s], (j / AY_NSTG) & 1))) {
+            if (!__all_sync(0xffffffffu, (mbar_test(&stg_full[s], (j / AY_NSTG) & 1) || mbar_wait(&stg_full[s], (j / AY_NSTG) & 1)))) {
                 fail(15);
                 break;
             }
-            if (j >= AY_NOP && !__all_sync(0xffffffffu, mbar_wait(&op_free[o], ((j / AY_NOP) - 1) & 1))) {
+            if (j >= AY_NOP && !__all_sync(0xffffffffu, (mbar_test(&op_free[o], ((j / AY_NOP) - 1) & 1) || mbar_wait(&op_free[o], ((j / AY_NOP) - 1) & 1)))) {
                 fail(16);
                 break;
             }
