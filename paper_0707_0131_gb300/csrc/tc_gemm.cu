@@ -10,8 +10,10 @@
 // swizzle), the B tile is written by the threads from the RHS-inner field.
 //
 // Precision.  kind::tf32 keeps 10 mantissa bits, so each operand is split into
-// hi = (x with its low 13 mantissa bits cleared) and lo = x - hi, and D =
-// hi*hi + hi*lo + lo*hi (three MMAs per K step): products at about FP32 accuracy.
+// hi = (x with its low 13 mantissa bits cleared) and lo = x - hi, and D = A_hi B +
+// A_lo B with B = [B_hi B_lo] taken as one operand of width 2N (B_lo's rows follow
+// B_hi's), two MMAs per K step whose halves are added when drained: products at about
+// FP32 accuracy.
 // The tensor pipe's own FP32 accumulation loses accuracy with the length of the
 // sum (measured at 10.6M complex rows: relative error 1e-6 after 2 K tiles per
 // accumulator, 3e-5 after 128), so TMEM holds two accumulators used by alternate
@@ -204,19 +206,27 @@ static_assert((KT / 2) * 16 <= 32 * WORKERS, "one B value per worker thread per 
 // Worker warp w (warps 2..9) drains TMEM lanes 32 (w % 4) .. + 31 (the lane quarter a
 // warp may access) and the half h = (w - 2) / 4 of the region's MT * N columns.
 template <int MT, int N>
+// A region holds, for M tile mt, A_mt B_hi in columns mt 2N + [0, N) and A_mt B_lo in
+// mt 2N + N + [0, N); output column cc = mt N + c is the sum of the two.
 __device__ __forceinline__ void drain(uint32_t region, int quarter, int half, float *acc_hi, float *acc_lo) {
     constexpr int HC = MT * N / 2;
-    const uint32_t base = region + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * HC);
+    const uint32_t base = region + ((uint32_t)(quarter * 32) << 16);
 #pragma unroll
     for (int c0 = 0; c0 < HC; c0 += 8) {
-        uint32_t v[8];
+        const int cc = half * HC + c0, mt = cc / N, c = cc % N;
+        uint32_t v[8], w[8];
         asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
                      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
-                     : "r"(base + c0)
+                     : "r"(base + (uint32_t)(mt * 2 * N + c))
+                     : "memory");
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+                     : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]), "=r"(w[6]), "=r"(w[7])
+                     : "r"(base + (uint32_t)(mt * 2 * N + N + c))
                      : "memory");
         asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
-        for (int j = 0; j < 8; j++) two_sum_add(acc_hi[c0 + j], acc_lo[c0 + j], __uint_as_float(v[j]));
+        for (int j = 0; j < 8; j++)
+            two_sum_add(acc_hi[c0 + j], acc_lo[c0 + j], __uint_as_float(v[j]) + __uint_as_float(w[j]));
     }
 }
 
@@ -229,8 +239,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_ahb(const __grid_constant_
     constexpr uint32_t a_bytes = TM * KT * 4;  // 16 KB
     constexpr uint32_t b_bytes = (uint32_t)((N + 7) / 8) * 1024;
     constexpr uint32_t stage_bytes = 2 * MT * a_bytes + 2 * b_bytes;
-    constexpr uint32_t RCOLS = MT * N;
-    constexpr uint32_t NCOLS = NREG * RCOLS <= 32 ? 32 : (NREG * RCOLS <= 64 ? 64 : (NREG * RCOLS <= 128 ? 128 : 256));
+    constexpr uint32_t RCOLS = MT * 2 * N;  // per M tile: A B_hi, then A B_lo (drain adds them)
+    constexpr uint32_t NCOLS =
+        NREG * RCOLS <= 32 ? 32 : (NREG * RCOLS <= 64 ? 64 : (NREG * RCOLS <= 128 ? 128 : (NREG * RCOLS <= 256 ? 256 : 512)));
+    static_assert(NREG * RCOLS <= 512, "TMEM columns");
     __shared__ __align__(8) uint64_t raw_full[NS], split_done[NS], stage_free[NS], acc_full[NREG], acc_empty[NREG],
         done, never;
     __shared__ uint32_t tmem_base;
@@ -286,9 +298,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_ahb(const __grid_constant_
             int kt = 0;
             for (; kt < nkt && !abort_flag; kt++) {
                 const int s = kt % NS;
-                if (kt >= NS && !mbar_wait(&stage_free[s], ((kt / NS) - 1) & 1)) {
-                    fail(1);
-                    break;
+                if (kt >= NS) {
+                    const unsigned pf = ((kt / NS) - 1) & 1;
+                    if (!mbar_test(&stage_free[s], pf) && !mbar_wait(&stage_free[s], pf)) {
+                        fail(1);
+                        break;
+                    }
                 }
                 mbar_expect_tx(&raw_full[s], MT * a_bytes);
                 for (int mt = 0; mt < MT; mt++) tma_load_2d(A_hi(s, mt), &tmap, (kt0 + kt) * KT, mt * TM, &raw_full[s]);
@@ -298,31 +313,36 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_ahb(const __grid_constant_
     } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
-            const uint32_t idesc = idesc_tf32(TM, N);
+            const uint32_t idesc = idesc_tf32(TM, 2 * N);
             for (int kt = 0; kt < nkt && !abort_flag; kt++) {
                 const int s = kt % NS, g = kt / FLUSH;
-                if (!mbar_wait(&split_done[s], (kt / NS) & 1)) {
+                const unsigned ps = (kt / NS) & 1;
+                if (!mbar_test(&split_done[s], ps) && !mbar_wait(&split_done[s], ps)) {
                     fail(2);
                     break;
                 }
-                if (kt % FLUSH == 0 && g >= NREG && !mbar_wait(&acc_empty[g % NREG], ((g / NREG) - 1) & 1)) {
-                    fail(3);
-                    break;
+                if (kt % FLUSH == 0 && g >= NREG) {
+                    const unsigned pe = ((g / NREG) - 1) & 1;
+                    if (!mbar_test(&acc_empty[g % NREG], pe) && !mbar_wait(&acc_empty[g % NREG], pe)) {
+                        fail(3);
+                        break;
+                    }
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
                 // descriptors of the stage's tiles; a K step of 8 tf32 (32 bytes along the
                 // swizzled row) adds 2 to the start-address field
-                const uint64_t bh0 = sdesc(sa(B_hi(s))), bl0 = sdesc(sa(B_lo(s)));
+                // B_lo's rows follow B_hi's: one MMA of width 2N takes A [B_hi B_lo]; per K step
+                // A_hi [B_hi B_lo] + A_lo [B_hi B_lo] (the lo x lo term is below FP32 rounding)
+                const uint64_t b0 = sdesc(sa(B_hi(s)));
 #pragma unroll
                 for (int mt = 0; mt < MT; mt++) {
-                    const uint32_t d = region(g) + mt * N;
+                    const uint32_t d = region(g) + mt * 2 * N;
                     const uint64_t ah0 = sdesc(sa(A_hi(s, mt))), al0 = sdesc(sa(A_lo(s, mt)));
 #pragma unroll
                     for (int ks = 0; ks < KT / 8; ks++) {
                         const uint64_t o = 2 * ks;
-                        mma_tf32(d, ah0 + o, bh0 + o, idesc, (kt % FLUSH != 0 || ks > 0) ? 1 : 0);
-                        mma_tf32(d, ah0 + o, bl0 + o, idesc, 1);
-                        mma_tf32(d, al0 + o, bh0 + o, idesc, 1);
+                        mma_tf32(d, ah0 + o, b0 + o, idesc, (kt % FLUSH != 0 || ks > 0) ? 1 : 0);
+                        mma_tf32(d, al0 + o, b0 + o, idesc, 1);
                     }
                 }
                 mma_commit(&stage_free[s]);
@@ -455,12 +475,13 @@ __global__ void k_tc_reduce(const double *partials, int grid, int MT, int N, int
 // Out = beta Out + A Y on the tensor cores (the U y of Eq. 1 and the basis updates of
 // the growth step): D[n, (c, e)] = sum over K = (a, e') of A'[n, K] Yt[K, (c, e)], with
 // M = 128 complex rows per tile, K = 2 * 16 basis columns per chunk (re, im of each)
-// and N = 2k interleaved (re, im) output columns.  Each 1 KB column segment of A is
-// brought into shared memory by a bulk copy (a 3-deep ring, so that the copies of the
-// next chunks are in flight), then transposed to the K-major 128-byte-swizzled layout
-// the MMA reads while being split into TF32 hi and lo parts.  Yt is rebuilt per
-// chunk from Y (FP64 -> FP32 -> hi, lo).  K <= 512, so one TMEM accumulator per tile
-// stays at FP32-product accuracy without draining.
+// and N = 2k interleaved (re, im) output columns.  A job (one chunk of one tile) lands
+// in shared memory as [16 columns][128 rows]: one 2D TMA copy when A's columns are
+// evenly spaced, else one bulk copy per 1 KB column segment (window slots).  Worker
+// threads read their row, split it into TF32 hi and lo and store both into tensor
+// memory, where the MMAs read A (no shared-memory round trip for the split operand);
+// Yt, split the same way, is built once per launch (k_ay_prep_b).  K <= 512, so one
+// TMEM accumulator per tile stays at FP32-product accuracy without draining.
 // ------------------------------------------------------------------------------------
 template <int N>
 struct AyStages {  // staging ring depth (copies in flight): 208 KB of shared memory with the B buffers
