@@ -380,6 +380,7 @@ def run_serve(a):
     grow = [srv.submit(s_.key, rhs_of(s_.key, j)) for j in range(n_grow) for s_ in specs]
     grow_res = [f.result() for f in grow]
     grow_wall = time.perf_counter() - t0
+    print(f"serve: growth phase {len(grow_res)} requests in {grow_wall:.1f} s", file=sys.stderr, flush=True)
     grow_lat = srv.percentiles()
     # phase 2, capacity: a burst of max_rhs requests per operator (one full batch each)
     srv.latencies.clear()
@@ -390,6 +391,8 @@ def run_serve(a):
         f.result()
     cap = len(burst) / (time.perf_counter() - t0)
     rate = 0.8 * cap
+    print(f"serve: capacity {cap:.1f} RHS/s from a burst of {len(burst)}; Poisson at {rate:.1f}/s",
+          file=sys.stderr, flush=True)
     # phase 3, timed: Poisson arrivals at 0.8x that capacity; latencies and batch sizes are
     # taken from this phase only
     srv.latencies.clear()

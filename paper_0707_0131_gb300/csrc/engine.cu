@@ -48,6 +48,14 @@ static thread_local std::string g_last_error;
         if (e_ != cudaSuccess) throw Error{EIG_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)}; \
     } while (0)
 
+// Graph captures and device-wide synchronisation exclude each other: a
+// cudaDeviceSynchronize, cudaFree or cudaFreeHost (both may synchronise the device)
+// issued by one thread while another thread's stream is being captured fails and
+// invalidates that capture, which happens when several operators are served from their
+// own threads.  Captures hold this lock, and so does every device-wide sync and free
+// (recursive: a destroy holds it over the sync and the frees of its buffers).
+static std::recursive_mutex g_capture_mu;
+
 struct DevBuf {
     void *p = nullptr;
     size_t n = 0;
@@ -71,7 +79,10 @@ struct DevBuf {
         if (bytes > n) alloc(bytes);
     }
     void release() {
-        if (p) cudaFree(p);
+        if (p) {
+            std::lock_guard<std::recursive_mutex> cap_lock(g_capture_mu);
+            cudaFree(p);
+        }
         p = nullptr;
         n = 0;
     }
@@ -87,7 +98,10 @@ struct PinBuf {
     size_t n = 0;
     void ensure(size_t bytes) {
         if (bytes <= n) return;
-        if (p) cudaFreeHost(p);
+        if (p) {
+            std::lock_guard<std::recursive_mutex> cap_lock(g_capture_mu);
+            cudaFreeHost(p);
+        }
         p = nullptr;
         n = 0;
         if (cudaMallocHost(&p, bytes) != cudaSuccess) {
@@ -98,7 +112,10 @@ struct PinBuf {
         n = bytes;
     }
     ~PinBuf() {
-        if (p) cudaFreeHost(p);
+        if (p) {
+            std::lock_guard<std::recursive_mutex> cap_lock(g_capture_mu);
+            cudaFreeHost(p);
+        }
     }
     template <typename T>
     T *as() const {
@@ -718,6 +735,7 @@ static cudaGraphExec_t cg_graph(Solve &sv, eig_op_s *op) {
     // cannot be captured); the graph is launched on the caller's stream
     cudaStream_t s = op->cap_stream;
     cudaGraph_t graph = nullptr;
+    std::lock_guard<std::recursive_mutex> cap_lock(g_capture_mu);
     CUDA_CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     prof_record_begin(&gr.rec);
     cudaError_t e = cudaSuccess;
@@ -1398,7 +1416,10 @@ eig_status eig_op_create(const double *gauge, const int dims[4], double m_q, con
             CUDA_CK(launch_pack_gauge(stage.as<double>(), op->gauge_alt.p, op->gf_alt, V, 0));
         }
     }
-    CUDA_CK(cudaDeviceSynchronize());
+    {
+        std::lock_guard<std::recursive_mutex> cap_lock(g_capture_mu);
+        CUDA_CK(cudaDeviceSynchronize());
+    }
     ensure_workspace(op.get());
     op->st.alloc(sizeof(CGScalars) * MAX_RHS);
     op->st_h.ensure(sizeof(CGScalars) * MAX_RHS);
@@ -1413,6 +1434,7 @@ eig_status eig_op_create(const double *gauge, const int dims[4], double m_q, con
 eig_status eig_op_destroy(eig_op op) {
     API_BEGIN
     if (op) {
+        std::lock_guard<std::recursive_mutex> cap_lock(g_capture_mu);
         cudaDeviceSynchronize();
         delete op;
     }
@@ -1423,6 +1445,7 @@ eig_status eig_op_trim(eig_op op, size_t *freed) {
     API_BEGIN
     ARG_CHECK(op, "null argument");
     std::lock_guard<std::mutex> lk(op->mu);
+    std::lock_guard<std::recursive_mutex> cap_lock(g_capture_mu);  // held over the sync and the frees
     CUDA_CK(cudaDeviceSynchronize());
     size_t bytes = 0;
     for (const FieldBuf *f : {&op->r, &op->p, &op->u, &op->b64, &op->x64, &op->u64, &op->xlo, &op->r64, &op->rsv,
@@ -1512,6 +1535,7 @@ eig_status eig_basis_create(eig_op op, int max_vecs, eig_basis *out) {
 eig_status eig_basis_destroy(eig_basis basis) {
     API_BEGIN
     if (basis) {
+        std::lock_guard<std::recursive_mutex> cap_lock(g_capture_mu);
         cudaDeviceSynchronize();
         delete basis;
     }

@@ -17,8 +17,9 @@ and deflation basis, the state the incremental method builds up) and its
 workspace (Krylov fields, staging, the eigCG window).  An operator is activated
 when its workspace (and, the first time, its resident part) fits next to what is
 held; otherwise idle operators give their workspace back (eig_op_trim, the basis
-stays), and only if that is not enough is the least recently used idle operator
-closed and its basis dropped.
+stays); while the workspaces of busy operators would make room once they are done, the
+request waits for them; only when even that is not enough is the least recently used
+idle operator closed and its basis dropped.
 
 This module only schedules calls; all arithmetic runs in libeigcg.so.
 """
@@ -178,27 +179,33 @@ class _Worker:
         import torch
 
         s = self.spec
-        with torch.cuda.stream(self.stream):
-            if self.use_eigcg(self.basis.size):
-                b = torch.from_numpy(req.b).to("cuda", non_blocking=False)
-                x = torch.zeros_like(b)
-                st = self.op.eigcg_solve(b, x, s.nev, s.m, s.tol, basis=self.basis, stream=self.stream)
-                self.basis.grow(stream=self.stream)
-                if self.policy is not None:
-                    self.policy.record(st["iters"])
-                self._finish([req], x.reshape(1, -1), [st], "eigcg")
-                return
-            batch = self._take(req, s.max_rhs)
-            k = 1
-            while k < len(batch):
-                k *= 2
-            B = np.zeros((k, req.b.size), dtype=np.complex128)
-            for i, r in enumerate(batch):
-                B[i] = r.b
-            Bd = torch.from_numpy(B).to("cuda")
-            Xd = torch.zeros_like(Bd)
-            sts = self.op.initcg_solve(Bd, Xd, s.tol, s.restart_tol, basis=self.basis, k=k, stream=self.stream)
-            self._finish(batch, Xd, sts[: len(batch)], "initcg")
+        batch = [req]
+        try:
+            with torch.cuda.stream(self.stream):
+                if self.use_eigcg(self.basis.size):
+                    b = torch.from_numpy(req.b).to("cuda", non_blocking=False)
+                    x = torch.zeros_like(b)
+                    st = self.op.eigcg_solve(b, x, s.nev, s.m, s.tol, basis=self.basis, stream=self.stream)
+                    self.basis.grow(stream=self.stream)
+                    if self.policy is not None:
+                        self.policy.record(st["iters"])
+                    self._finish([req], x.reshape(1, -1), [st], "eigcg")
+                    return
+                batch = self._take(req, s.max_rhs)
+                k = 1
+                while k < len(batch):
+                    k *= 2
+                B = np.zeros((k, req.b.size), dtype=np.complex128)
+                for i, r in enumerate(batch):
+                    B[i] = r.b
+                Bd = torch.from_numpy(B).to("cuda")
+                Xd = torch.zeros_like(Bd)
+                sts = self.op.initcg_solve(Bd, Xd, s.tol, s.restart_tol, basis=self.basis, k=k, stream=self.stream)
+                self._finish(batch, Xd, sts[: len(batch)], "initcg")
+        except Exception as e:  # the requests of this call fail; the worker serves the next ones
+            for r in batch:
+                if not r.future.done():
+                    r.future.set_exception(e)
 
     def _finish(self, batch, X, sts, kind):
         X = X.cpu().numpy()
@@ -253,6 +260,13 @@ class Server:
                     victim.trim()
                     self.used -= victim.spec.workspace_bytes()
                     self.trims += 1
+                    continue
+                # a basis is the work of all the eigCG solves that grew it: rather than close
+                # one, wait while the workspaces of busy operators would make room once freed
+                busy_ws = sum(o.spec.workspace_bytes() for o in self.workers.values()
+                              if o is not w and o.active and o.spec.prebuilt is None)
+                if busy_ws > 0 and self.used - busy_ws + need <= self.budget:
+                    self.cv.wait(timeout=0.05)
                     continue
                 resident_idle = [o for o in idle if o.resident and not o.active]
                 if resident_idle:

@@ -169,3 +169,42 @@ def test_trim_keeps_basis(serving):
         assert _check(spec, B[r], X1[r], 1e-8)
     basis.close()
     op.close()
+
+
+def test_trim_while_another_thread_captures(serving):
+    """Two operators served from two threads, each on its own stream: every round one
+    thread trims its operator (device-wide sync and frees) while the other may be capturing
+    the CG graph of its next solve (a trimmed operator captures its graphs again).  Trims
+    and captures exclude each other inside the library, so neither call fails and every
+    solve reaches its tolerance."""
+    import threading
+
+    import torch
+
+    from paper_0707_0131_gb300.api import Op
+
+    spec = _specs(serving)[1]
+    errors, done = [], []
+
+    def worker(seed):
+        try:
+            stream = torch.cuda.Stream()
+            op = Op(spec.gauge, spec.dims, spec.m_q, prec=32, max_rhs=4)
+            B = np.stack([fx.make_rhs(spec.dims, seed + i)[0].reshape(-1) for i in range(4)])
+            for _ in range(12):
+                X = np.zeros_like(B)
+                sts = op.initcg_solve(B, X, tol=1e-8, k=4, stream=stream)
+                assert all(_check(spec, B[r], X[r], 1e-8) for r in range(4)), [s_["iters"] for s_ in sts]
+                op.trim()
+            op.close()
+            done.append(seed)
+        except Exception as e:  # reported below; the other thread keeps going
+            errors.append(repr(e))
+
+    threads = [threading.Thread(target=worker, args=(9500 + 100 * i,)) for i in range(2)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join(timeout=600)
+    assert not errors, errors
+    assert len(done) == 2

@@ -1,6 +1,7 @@
 """Host logic of the serving loop (no GPU): admission under the HBM budget first takes
-workspaces back from idle operators (their bases stay), then closes the least recently
-used idle operator, waits while the others are busy, skips operators with queued
+workspaces back from idle operators (their bases stay), waits while busy operators'
+workspaces would make room, only then closes the least recently used idle operator,
+skips operators with queued
 requests, and the Poisson arrival generator and latency percentiles behave as stated."""
 import queue
 import threading
@@ -106,6 +107,34 @@ def test_admission_waits_for_busy_operators():
     assert b.active and not a.active and a.resident and srv.used == 80
 
 
+def test_admission_waits_for_a_busy_workspace_before_closing_a_basis():
+    # a busy (resident 20 + workspace 40), c resident but trimmed (30), budget 130: b needs 60.
+    # Closing c would make room at once, but a's workspace will too once a is done, so b
+    # waits and c keeps its basis.
+    a, b, c = _FakeWorker("a", 20, 40, 1.0), _FakeWorker("b", 20, 40, 2.0), _FakeWorker("c", 30, 10, 0.5)
+    srv = _server(130, [a, b, c])
+    srv._admit(c)
+    c.trim()
+    srv.used -= 10
+    srv._admit(a)
+    a.busy = True
+    assert srv.used == 90
+
+    def release():
+        time.sleep(0.2)
+        a.busy = False
+        srv._released()
+
+    th = threading.Thread(target=release)
+    th.start()
+    t0 = time.perf_counter()
+    srv._admit(b)
+    th.join()
+    assert time.perf_counter() - t0 >= 0.15
+    assert b.active and not a.active and a.resident and c.resident and "close" not in c.events
+    assert srv.closes == 0 and srv.used == 110
+
+
 def test_admission_skips_operators_with_queued_requests():
     a, b, c = _FakeWorker("a", 10, 40, 1.0), _FakeWorker("b", 10, 40, 2.0), _FakeWorker("c", 10, 40, 3.0)
     srv = _server(110, [a, b, c])
@@ -134,3 +163,25 @@ def test_operator_larger_than_budget_is_refused():
         assert "budget" in str(e)
     else:
         raise AssertionError("an operator above the budget must be refused")
+
+
+def test_failed_solve_fails_its_requests_and_the_worker_goes_on():
+    """A solve that raises (here: no GPU to copy the batch to) sets the exception on every
+    request of its batch instead of ending the worker thread, so that no caller waits on
+    a future that never completes."""
+
+    class _Basis:
+        size = 100
+
+    spec = serving.OpSpec(key="x", dims=(4, 4, 4, 4), m_q=0.1, gauge=None, max_rhs=4, nev=4, m=12, basis_max=8)
+    w = serving._Worker.__new__(serving._Worker)
+    w.spec, w.q, w.stream, w.basis, w.op = spec, queue.Queue(), None, _Basis(), None
+    w.policy, w.growing = None, False
+    reqs = [serving.Request("x", np.ones(8, dtype=np.complex128)) for _ in range(3)]
+    for r in reqs[1:]:
+        w.q.put(r)
+    w._serve(reqs[0])  # must not raise
+    assert all(r.future.done() and r.future.exception() is not None for r in reqs)
+    again = serving.Request("x", np.ones(8, dtype=np.complex128))
+    w._serve(again)
+    assert again.future.exception() is not None
