@@ -346,21 +346,22 @@ def run_serve(a):
     by_key = {s.key: s for s in specs}
     rng = np.random.default_rng(105)
     keys = [specs[i].key for i in rng.integers(0, len(specs), size=a.requests)]
-    rhs_cache = {}
+    # eight Gaussian RHS per operator, generated once before anything is timed (requests
+    # reuse them in turn)
+    rhs_cache = {s_.key: [fx.make_rhs(s_.dims, 4_000_000 + j)[0].reshape(-1) for j in range(8)] for s_ in specs}
+
+    def rhs_of(key, j):
+        return rhs_cache[key][j % 8]
 
     def rhs(i):
-        key = keys[i]
-        if key not in rhs_cache:
-            rhs_cache[key] = [fx.make_rhs(by_key[key].dims, 4_000_000 + j)[0].reshape(-1) for j in range(8)]
-        return rhs_cache[key][i % 8]
+        return rhs_of(keys[i], i)
 
     # plain FP64 eigCG per request (same GPU, no deflation, no batching): one solve per operator
     plain_ms = {}
     if not a.no_plain:
         for s_ in specs:
             op64 = Op(s_.gauge, s_.dims, s_.m_q, prec=64)
-            b = torch.from_numpy(rhs_cache.setdefault(s_.key, [fx.make_rhs(s_.dims, 4_000_000 + j)[0].reshape(-1)
-                                                               for j in range(8)])[0]).cuda()
+            b = torch.from_numpy(rhs_of(s_.key, 0)).cuda()
             x = torch.zeros_like(b)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -368,9 +369,6 @@ def run_serve(a):
             torch.cuda.synchronize()
             plain_ms[s_.key] = (time.perf_counter() - t0) * 1e3
             op64.close()
-    def rhs_of(key, j):
-        return rhs_cache.setdefault(key, [fx.make_rhs(by_key[key].dims, 4_000_000 + q)[0].reshape(-1)
-                                          for q in range(8)])[j % 8]
 
     srv = serving.Server(specs, hbm_budget_bytes=a.budget_gb * 1e9)
     # phase 1, growth: each operator serves the requests that grow its basis to basis_max
