@@ -906,12 +906,21 @@ static bool cg_run(Solve &sv, int max_iter, Window *w, eig_op_s *op) {
                 const long fs = (long)op->Vf * 12;
                 for (int a = 0; a < m; a++) off[a] = (long)w->slots[a] * fs;
                 CUDA_CK(cudaMemcpyAsync(op->col_off.p, off.data(), m * sizeof(long), cudaMemcpyHostToDevice, s));
-                std::vector<double> qz((size_t)m * nout * 2);
-                for (int a = 0; a < m; a++)
+                // tensor-core path: A is the whole window (m + 1 evenly spaced slots, one 2D TMA
+                // copy per tile chunk) and QZ's rows are placed at the slots of their columns; the
+                // spare slot (this iteration's vector, written above) gets zero coefficients.  All
+                // m + 1 slots were written during this solve, so none holds stale non-finite data.
+                const bool tcw = op->wprec != P64 && nout <= 32 && (op->ncomplex() % 2) == 0 && tc_gemm_enabled();
+                const int qrows = tcw ? m + 1 : m;
+                std::vector<double> qz((size_t)qrows * nout * 2, 0.0);
+                for (int a = 0; a < m; a++) {
+                    const size_t row = tcw ? (size_t)w->slots[a] : (size_t)a;
                     for (int c = 0; c < nout; c++) {
-                        qz[((size_t)a * nout + c) * 2] = QZ[(size_t)c * m + a].real();
-                        qz[((size_t)a * nout + c) * 2 + 1] = QZ[(size_t)c * m + a].imag();
+                        qz[(row * nout + c) * 2] = QZ[(size_t)c * m + a].real();
+                        qz[(row * nout + c) * 2 + 1] = QZ[(size_t)c * m + a].imag();
                     }
+                }
+                op->qz.ensure(qz.size() * sizeof(double));
                 CUDA_CK(cudaMemcpyAsync(op->qz.p, qz.data(), qz.size() * sizeof(double), cudaMemcpyHostToDevice, s));
                 ColSet Vw;
                 Vw.base = op->win.p;
@@ -922,13 +931,15 @@ static bool cg_run(Solve &sv, int max_iter, Window *w, eig_op_s *op) {
                 Vw.col_off = op->col_off.as<long>();
                 void *tp = w->tprev_is_a ? op->tprev.p : op->tcur.p;
                 void *tc = w->tprev_is_a ? op->tcur.p : op->tprev.p;
-                const bool tcw = !Vw.f64 && nout <= 32 && (op->ncomplex() % 2) == 0 && tc_gemm_enabled();
                 if (tcw) {
-                    // V <- V QZ on the tensor cores, in place (each CTA reads all m columns of
+                    // V <- V QZ on the tensor cores, in place (each CTA reads all m + 1 slots of
                     // its rows before writing them), then w^H V_new with w = t - beta t_prev
                     // formed on the fly
                     ColSet Out = Vw;
                     Out.ncols = nout;
+                    Vw.col_off = nullptr;
+                    Vw.col_stride = fs;
+                    Vw.ncols = m + 1;
                     op->tcerr.ensure(16);
                     op->errh.ensure(16);
                     CUDA_CK(cudaMemsetAsync(op->tcerr.p, 0, 16, s));
@@ -1673,21 +1684,28 @@ static eig_status eigcg_impl(eig_op op, eig_basis basis, const double *b, double
             const long fs = op->ncomplex();
             for (int a = 0; a < w.i; a++) off[a] = (long)w.slots[a] * fs;
             CUDA_CK(cudaMemcpyAsync(op->col_off.p, off.data(), w.i * sizeof(long), cudaMemcpyHostToDevice, s));
-            std::vector<double> yr((size_t)w.i * nr * 2);
-            for (int a = 0; a < w.i; a++)
+            // after a restart every one of the m + 1 slots was written during this solve: then A
+            // is the whole window, evenly spaced (one 2D TMA copy per tile chunk on the tensor
+            // cores), with Y's rows placed at the slots of their columns and zeros elsewhere
+            const bool whole = w.restarts > 0;
+            const int yrows = whole ? w.m + 1 : w.i;
+            std::vector<double> yr((size_t)yrows * nr * 2, 0.0);
+            for (int a = 0; a < w.i; a++) {
+                const size_t row = whole ? (size_t)w.slots[a] : (size_t)a;
                 for (int c = 0; c < nr; c++) {
-                    yr[((size_t)a * nr + c) * 2] = Y[(size_t)c * w.i + a].real();
-                    yr[((size_t)a * nr + c) * 2 + 1] = Y[(size_t)c * w.i + a].imag();
+                    yr[(row * nr + c) * 2] = Y[(size_t)c * w.i + a].real();
+                    yr[(row * nr + c) * 2 + 1] = Y[(size_t)c * w.i + a].imag();
                 }
+            }
             basis->Y.ensure(yr.size() * sizeof(double));
             CUDA_CK(cudaMemcpyAsync(basis->Y.p, yr.data(), yr.size() * sizeof(double), cudaMemcpyHostToDevice, s));
             ColSet A;
             A.base = op->win.p;
             A.f64 = op->wprec == P64;
             A.ki = 1;
-            A.col_stride = 0;
-            A.ncols = w.i;
-            A.col_off = op->col_off.as<long>();
+            A.col_stride = whole ? fs : 0;
+            A.ncols = yrows;
+            A.col_off = whole ? nullptr : op->col_off.as<long>();
             ColSet O = field_cols(basis->pend.p, A.f64, 1, basis->fsize(), nr, false);
             ay_run(basis, A, basis->Y.as<double>(), O, 0.0, op->ncomplex(), s);
             sync(s);
