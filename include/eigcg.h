@@ -118,9 +118,12 @@ eig_status eig_op_apply(eig_op op, int which, const double *in, double *out, int
 
 /* The stencil launch the autotuner chose for k-RHS products of an FP32/FP16 op (the
  * matrix-vector product of Fig. 1 step 11, timed per shape on the first solve):
- * *variant 0..7 (0, 1: shared-memory staged loads of 1 or 2 RHS per thread; 2, 3, 7:
+ * *variant 0..21 (0, 1: shared-memory staged loads of 1 or 2 RHS per thread; 2, 3, 7:
  * direct loads of 1 RHS per thread at 4 or 5 resident blocks per SM, 7 with L1
- * prefetch; 4, 5, 6: direct loads of 2 RHS per thread, 6 with L1 prefetch) and
+ * prefetch; 4, 5, 6: direct loads of 2 RHS per thread, 6 with L1 prefetch; 8 + v:
+ * variant v over a tiled site order; 16, 17: two adjacent RHS per thread with 256-bit
+ * loads and the next hop's data in flight, at 2 or 3 resident blocks per SM; 18, 19:
+ * 16, 17 over the tiled order; 20, 21: 17, 19 with an L1 prefetch of the hop after next) and
  * *link_reals 12 or 18 (the resident FP32 link form used).  Both are -1 and 0 for FP64
  * ops or before the first solve with k RHS.  Odd-even ops report the half stencil.
  * Errors: EIG_ERR_ARG (null pointer, k not a power of two <= max_rhs). */
