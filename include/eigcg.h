@@ -104,7 +104,9 @@ eig_status eig_op_destroy(eig_op op);
  * staging, the eigCG window, the captured CG graphs) and keeps the links; bases bound to
  * the op keep their vectors and H.  The next call that needs the workspace allocates it
  * again.  For a serving loop that holds more operators' bases than it can give
- * workspaces at once (no counterpart in the paper).  Synchronises the device.  *freed
+ * workspaces at once (no counterpart in the paper).  Synchronises the device; other
+ * threads may meanwhile use other operators (inside the library this synchronisation and
+ * the frees wait for, and hold off, their CUDA-graph captures).  *freed
  * (may be NULL): bytes released.  Errors: EIG_ERR_ARG, EIG_ERR_CUDA; a later call may
  * return EIG_ERR_OOM when the workspace no longer fits. */
 eig_status eig_op_trim(eig_op op, size_t *freed);
